@@ -1,0 +1,347 @@
+"""Throughput benchmark of the biased neutron history loop on GB300.
+
+Default (one GPU): the powder-diffractometer workload -- 1.5 A beam 1 x 2 cm on
+a cylinder r = 0.5 cm, h = 2 cm of a synthetic fcc powder (18 Bragg lines) plus
+incoherent scattering, 1 mm can, 3600-bin 2-theta cylinder detector -- with
+1e8 histories per step in FP32 transport and FP64 tallies.  A step is one
+persistent launch that runs every history through source, flights, boundary
+crossings, collisions and scoring.  Beside it, the batched+adjoint workload
+(256 powder instances with uneven history counts, score-function gradients
+and the backward contraction) is timed, and both are compared at matched
+tally error.
+
+Prints one JSON line.  --impl reference times the CPU oracle instead (the
+reference arm of this project) on a bounded sample of the same workload."""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "histories/s on 1 GB300: plain vs batched+adjoint, at matched tally error"
+UNIT = "histories/s"
+POWDER_N = 100_000_000
+# Thread instructions the transport kernel executes per powder history (ncu,
+# smsp__thread_inst_executed.sum / histories, on the 1e6-history powder case):
+# the per-unit figure of the ALU roofline.
+INST_PER_HISTORY = None
+SM_COUNT = 152
+LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
+SM_MAX_MHZ = 2070.0
+
+
+def workload_desc(name: str):
+    import workloads as W
+    if name == "powder":
+        return W.powder(n_histories=POWDER_N), "powder diffractometer, 1e8 histories, FP32 transport"
+    if name == "guide":
+        return W.guide(n_histories=POWDER_N), "supermirror guide 20 m, 1e8 histories, FP32 transport"
+    if name == "slab":
+        return W.slab(g=3.0, n_histories=1_000_000), "slab, bias 3, 1e6 histories, FP64 transport"
+    if name == "imaging":
+        return W.imaging(n_histories=100_000_000), "CSG imaging 1000 primitives, 1e8 histories"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name: str, label: str, extra: dict) -> dict:
+    cfg = {"workload": label, "name": name, "l2": "flushed between timed steps (256 MiB write)"}
+    cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = Path(os.environ.get("TP_CLOCK_LOG", f"/tmp/tp_clocks_{os.getpid()}.csv"))
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if not self.proc or not self.path.exists():
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args, rank: int, world: int) -> dict | None:
+    import numpy as np
+    import torch
+    from paper_2304_06226_gb300 import build
+    build.build()
+    from paper_2304_06226_gb300.engine import Scene
+    import workloads as W
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    desc, label = workload_desc(args.workload)
+    if args.histories:
+        desc["instances"]["counts"][0] = args.histories
+        label = label.replace("1e8 histories", f"{args.histories:.0e} histories")
+    n = int(desc["instances"]["counts"][0])
+    sc = Scene(desc)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    first = rank * n   # disjoint history ids per rank: weak scaling
+
+    # ---- warm-up (also JIT-free: the library is ahead-of-time compiled) ----
+    for _ in range(args.warmup):
+        sc.run(n, first=first)
+    torch.cuda.synchronize()
+    sc.reset()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush_l2(flush)
+            ev[k][0].record(stream)
+            sc.run(n, first=first, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(kernel_ms) / 1e3
+    if dist:
+        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    counters = sc.counters()
+    tot = n * args.steps
+    value = world * tot / dev_s
+    # ---- tally error of the integrated detector total (per history) ----
+    raw = sc.raw(0)
+    N = float(tot)
+    mean_tot = raw["sum"].sum() / N
+    # rel. standard error of the integrated total: each history hits at most one bin
+    var = raw["sumsq"].sum() / N - mean_tot ** 2
+    rel_err = math.sqrt(max(var, 0.0) / (N - 1)) / mean_tot
+    fom_plain = 1.0 / (rel_err ** 2 * (dev_s / world))
+
+    # ---- end to end through the public API with host buffers ----
+    import ctypes as C
+    from paper_2304_06226_gb300 import native as NN
+    host_mean = np.empty(sc.total_bins)
+    host_err = np.empty(sc.total_bins)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        sc.reset()
+        sc.run(n, first=first)
+        for t in range(len(sc.tally_bins)):
+            o = sc.tally_off[t]
+            NN.tp_read_tallies(sc.handle, t, 0, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * n * e2e_steps / e2e_s
+    h2d = 2 * 8 * sc.n_inst + 8          # history counts, first ids, prefix (per run)
+    d2h = 2 * 8 * sc.total_bins          # means and standard errors
+
+    # ---- batched + adjoint ----
+    batched = None
+    if args.batched and rank == 0:
+        batched = run_batched(args, W, Scene, torch)
+
+    if rank != 0:
+        return None
+    inst_ph = INST_PER_HISTORY.get(args.workload) if isinstance(INST_PER_HISTORY, dict) else None
+    clocks = clk.summary()
+    peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    achieved = inst_ph * tot / (sum(kernel_ms) / 1e3) if inst_ph else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if sc.precision == "f32" else "f64",
+        "data": "synthetic",
+        "config": workload_config(args.workload, label, {
+            "histories_per_step_per_gpu": n, "tallies": "FP64 sum w, sum w^2 per bin",
+            "launch": {"block": sc.launch()[0], "ctas_per_sm": sc.launch()[1]},
+            "parallelism": f"history ids sharded over {world} GPU(s)"}),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "per_unit": inst_ph, "peak_basis": "152 SMs x 128 lanes x 2070 MHz"},
+        "kernel_ms": kernel_ms,
+        "tally": {"mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
+                  "counters": counters},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if batched:
+        line["batched_adjoint"] = batched
+        # matched error: time for each to reach the same relative error eps
+        eps = 1e-3
+        line["matched_error"] = {
+            "eps": eps,
+            "plain_s_to_eps": (rel_err / eps) ** 2 * tot / value,
+            "batched_s_to_eps_per_instance": batched.get("s_to_eps_per_instance"),
+        }
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, desc, n)
+    sc.close()
+    return line
+
+
+def run_batched(args, W, Scene, torch) -> dict:
+    """Workload 4: 256 instances, one persistent launch, gradients + backward."""
+    desc = W.batched()
+    sc = Scene(desc)
+    counts = sc.counts
+    total = int(counts.sum())
+    stream = torch.cuda.current_stream()
+    grad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda")
+    for _ in range(max(1, args.warmup // 2)):
+        sc.run(want_grad=True)
+    torch.cuda.synchronize()
+    sc.reset()
+    steps = max(1, args.batched_steps)
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fw_ms, bw_ms = [], []
+    for _ in range(steps):
+        a.record(stream)
+        sc.run(want_grad=True, stream=stream)
+        b.record(stream)
+        sc.backward(grad, stream=stream)
+        c.record(stream)
+        torch.cuda.synchronize()
+        fw_ms.append(a.elapsed_time(b))
+        bw_ms.append(b.elapsed_time(c))
+    t = (sum(fw_ms) + sum(bw_ms)) / 1e3
+    # matched error on the integrated total of a median-count instance
+    import numpy as np
+    q = int(np.argsort(counts)[len(counts) // 2])
+    raw = sc.raw(q)
+    N = float(counts[q]) * steps
+    m = raw["sum"].sum() / N
+    rel = math.sqrt(max(raw["sumsq"].sum() / N - m * m, 0.0) / (N - 1)) / m
+    hist_s = total * steps / t
+    sc.close()
+    return {"value": hist_s, "unit": UNIT, "instances": int(len(counts)), "histories_per_step": total,
+            "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
+            "rel_stderr_total_median_instance": rel,
+            "s_to_eps_per_instance": (rel / 1e-3) ** 2 * N / (hist_s / len(counts))}
+
+
+def cpu_baseline(args, desc, n_full) -> dict:
+    """The CPU oracle on the host cores, on a bounded sample of the workload."""
+    from oracle.oracle import OracleScene
+    cores = os.cpu_count() or 1
+    sc = OracleScene(desc)
+    sample = args.cpu_sample
+    sc.run(min(100_000, sample), threads=cores)       # warm the library
+    t0 = time.perf_counter()
+    sc.run(sample, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} histories of the {n_full}-history workload, FP64, {cores} threads",
+            "seconds": dt}
+
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    from oracle.oracle import OracleScene
+    desc, label = workload_desc(args.workload)
+    n = int(desc["instances"]["counts"][0])
+    cores = os.cpu_count() or 1
+    sc = OracleScene(desc)
+    per_step = args.ref_sample
+    for k in range(args.warmup):
+        sc.run(min(per_step, 200_000), first=k * per_step, threads=cores)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        sc.run(per_step, first=k * per_step, threads=cores)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": workload_config(args.workload, label, {"histories_per_step": per_step}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} histories per step of the {n}-history workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="powder")
+    ap.add_argument("--histories", type=int, default=0, help="override the histories per step")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-sample", type=int, default=40_000_000)
+    ap.add_argument("--ref-sample", type=int, default=10_000_000)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        line = run_ours(args, rank, world)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * tp.h -- C ABI of the GB300 (sm_103a) neutron history engine with
+ * probability-conserved cross-section biasing (arxiv 2304.06226).
+ *
+ * The problem (§2.1, Eq. eTransport): estimate detection probabilities
+ * f_det = integral of G f_src by Monte Carlo histories.  Each history (§3.1,
+ * "Simulation flow") is born at a particle gun (§3.2), is located in a volume of
+ * a CSG geometry (§3.3), samples a flight length from the *biased* macroscopic
+ * cross section Sigma_g = sum_i g_i Sigma_i (§2.4, Eq. eStepLength2), moves to the
+ * boundary (relocation) or to an interaction point, multiplies its weight by the
+ * true-to-biased likelihood ratio (§2.4, Eq. eWeight), is reflected by
+ * supermirrors (§2.5, Eqs. eMirrowRef and eMirrowNewDir), scatters (isotropic
+ * incoherent, Eq. eIncEla; powder Bragg lines, Eq. eCohEla) or is absorbed
+ * (1/v law, §2.2), and is scored at particle-tracing states ENTRY / EXIT (§3.4).
+ *
+ * Conventions (every call):
+ *  - No call aborts or throws.  Every call returns a tp_status; on failure
+ *    tp_last_error() gives a message (thread-local, valid until the next call on
+ *    the same thread).  A status other than TP_OK leaves the scene usable unless
+ *    it is TP_ERR_CUDA (the CUDA context may then be unusable).
+ *  - Input arrays are copied; the caller keeps ownership and may free them
+ *    after the call returns.
+ *  - Outputs go to caller-owned buffers, on the host or on the device as the
+ *    `on_device` flag of the call says.
+ *  - GPU work is ordered on the CUDA stream passed in tp_run.stream (the
+ *    caller's current stream).  Host-output calls synchronise that stream.
+ *  - Units: cm, Angstrom, 1/cm, barn, Angstrom^3, radians.
+ *  - The library allocates its own device memory (cudaMalloc) for a scene.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tp_scene tp_scene; /* opaque, library-owned */
+
+typedef enum {
+  TP_OK = 0,
+  TP_ERR_INVALID_ARG = 1, /* a bad argument or description (message says which) */
+  TP_ERR_GEOMETRY = 2,    /* overlapping primitives, primitive outside the world */
+  TP_ERR_CUDA = 3,        /* a CUDA runtime error */
+  TP_ERR_OOM = 4,         /* device allocation failed */
+  TP_ERR_TIMEOUT = 5,     /* a device-side wait or iteration cap gave up */
+  TP_ERR_STATE = 6        /* call out of order (e.g. run before tp_set_materials) */
+} tp_status;
+
+/* Solids (Appendix A: Box, Tube, Orb/Sphere with full phi). */
+enum { TP_BOX = 0, TP_TUBE = 1, TP_SPHERE = 2 };
+/* Volume roles: transport inside; terminal scorer volume; terminal absorber. */
+enum { TP_ROLE_BULK = 0, TP_ROLE_DETECTOR = 1, TP_ROLE_BLACK = 2 };
+/* Processes, in the order they are sampled. */
+enum { TP_PROC_ABS = 0, TP_PROC_INC = 1, TP_PROC_BRAGG = 2, TP_NPROC = 3 };
+/* Scorers (§3.4, Table tableScorer): a count, Angular, PSD (x,y), and a
+ * wavelength x position monitor (WlSpectrum crossed with a PSD axis). */
+enum { TP_TALLY_COUNT = 0, TP_TALLY_ANGULAR = 1, TP_TALLY_PSD = 2, TP_TALLY_WLX = 3 };
+/* Particle tracing states that trigger scorers (§3.4). */
+enum { TP_PTS_ENTRY = 0, TP_PTS_EXIT = 1 };
+/* Differentiable instance parameters. */
+enum { TP_PAR_RADIUS = 0, TP_PAR_SCALE = 1, TP_PAR_DENSITY = 2 };
+/* Particle guns (§3.2): a pencil (SimpleThermalGun with a fixed direction) and a
+ * rectangle emitting along +z (a moderator surface, UniModeratorGun-like). */
+enum { TP_SRC_PENCIL = 0, TP_SRC_RECT = 1 };
+/* Transport arithmetic. */
+enum { TP_FP32 = 0, TP_FP64 = 1 };
+
+#define TP_MAX_PARAMS 4
+#define TP_MAX_TALLIES 16
+
+/* One CSG primitive, placed in the world with no rotation.
+ * shape TP_BOX: params = half extents (x, y, z).
+ * shape TP_TUBE: params = (rmin, rmax, half height), axis 0/1/2 = x/y/z.
+ * shape TP_SPHERE: params = (rmin, rmax, unused).
+ * material: index into tp_set_materials' array, -1 = vacuum.
+ * mirror: index into tp_scene_desc.mirrors or -1.  A neutron arriving at the
+ *   boundary of a mirror primitive is reflected (§2.5) and never enters it.
+ * bind_rmin / bind_rmax: the radius moves with the TP_PAR_RADIUS instance
+ *   parameter, by (value - radius_nominal). */
+typedef struct {
+  int shape, axis, material, role, mirror, bind_rmin, bind_rmax;
+  double centre[3];
+  double params[3];
+} tp_prim;
+
+/* Supermirror (§2.5, Eq. eMirrowRef, Table tableMirror): m, R0, Qc (1/A),
+ * alpha (A), W (1/A). */
+typedef struct { double m, R0, Qc, alpha, W; } tp_mirror;
+
+/* A scorer.  kind TP_TALLY_ANGULAR bins the angle between (position - origin)
+ * and axis over [lo[0], hi[0]) in nbins[0] bins; TP_TALLY_PSD bins x over
+ * [lo[0],hi[0]) and y over [lo[1],hi[1]); TP_TALLY_WLX bins the wavelength over
+ * [lo[0],hi[0]) and x over [lo[1],hi[1]).  Bins are laid out axis-0 major.
+ * trigger TP_PTS_ENTRY / TP_PTS_EXIT of `volume` (primitive index, -1 = world).
+ * face: -1 any, else the face id (box 2*axis + (1 for the + face); tube 0
+ *   outer, 1 inner, 2 -cap, 3 +cap; sphere 0 outer, 1 inner).
+ * scat: -1 any, else only neutrons scattered exactly `scat` times (the
+ *   scatnum filter of the DeltaMomentum scorer, Appendix C). */
+typedef struct {
+  int kind, trigger, volume, face, scat;
+  int nbins[2];
+  double lo[2], hi[2];
+  double origin[3], axis[3];
+} tp_tally_desc;
+
+/* Source.  TP_SRC_PENCIL: at centre, direction +z.  TP_SRC_RECT: uniform on the
+ * rectangle centre +- half (x, y), direction +z tilted by angles uniform in
+ * +-div (x, y).  Wavelength uniform on [lambda_lo, lambda_hi].  With
+ * has_aperture, neutrons born outside centre +- aperture are stopped. */
+typedef struct {
+  int kind;
+  double centre[3];
+  double half[2];
+  double lambda_lo, lambda_hi;
+  double div[2];
+  int has_aperture;
+  double aperture[2];
+} tp_source;
+
+/* Scene description.  The world is a vacuum box (params = half extents) or
+ * sphere (params = (0, radius, 0)) containing every primitive; leaving it ends
+ * a history (EXIT of volume -1).  Primitives must not overlap (touching is
+ * allowed).  inst_params is [n_instances][n_params]; param_kind[n_params]. */
+typedef struct {
+  int world_shape;
+  double world_centre[3], world_params[3];
+  int n_prims;     const tp_prim* prims;
+  int n_mirrors;   const tp_mirror* mirrors;
+  tp_source source;
+  int n_tallies;   const tp_tally_desc* tallies;
+  int n_instances; const double* inst_params;
+  int n_params;    const int* param_kind;
+  double radius_nominal;
+  int precision;   /* TP_FP32 | TP_FP64 */
+  int event_cap;   /* events per history before it is truncated (counted); 0 = 4096 */
+} tp_scene_desc;
+
+/* Creates a scene: validates the description (TP_ERR_INVALID_ARG,
+ * TP_ERR_GEOMETRY) and uploads it to the current CUDA device.  *out receives a
+ * library-owned handle, freed by tp_destroy_scene. */
+tp_status tp_create_scene(const tp_scene_desc* desc, tp_scene** out);
+
+/* Material macroscopic cross sections (§2.2, §2.3):
+ *   absorption Sigma_a(lambda) = sigma_abs_ref * lambda/1.8 (abs_1v = 1, the
+ *     1/v law with the reference at 1.8 A) or sigma_abs_ref (abs_1v = 0);
+ *   isotropic incoherent elastic sigma_inc (Eq. eIncEla);
+ *   powder Bragg lines (Eq. eCohEla averaged over orientations):
+ *     Sigma(lambda) = lambda^2/(2 V0^2) sum_{2 d_i >= lambda} mult_i F2_i d_i
+ *     with d in A, F2 = |F|^2 in barn per cell, V0 in A^3.
+ * density_param / scale_param: instance parameter index multiplying every
+ *   process / the Bragg term, or -1.  Lines may come in any order.
+ * Replaces previous materials; resets bias factors to 1. */
+typedef struct {
+  double sigma_abs_ref;
+  int abs_1v;
+  double sigma_inc;
+  int n_lines;
+  double V0;
+  const double* d;
+  const double* mult;
+  const double* F2;
+  int density_param, scale_param;
+} tp_material;
+
+tp_status tp_set_materials(tp_scene* s, const tp_material* m, int n);
+
+/* Per-process bias factors g[TP_NPROC] of one material (§3.5: scatter_bias,
+ * abs_bias; §2.4): flights are sampled from sum_i g_i Sigma_i and the weight is
+ * compensated by Eq. eWeight.  g_i >= 0; g_i = 0 removes process i from the
+ * sampling (its Sigma still attenuates the weight); 1 = unbiased. */
+tp_status tp_set_bias(tp_scene* s, int material, const double g[TP_NPROC]);
+
+/* Optional per-history record (first collision, final state), written for
+ * histories of instance 0 with history id < n_records. */
+typedef struct {
+  double first_collision[3];
+  double dir_after_first[3];
+  double final_pos[3];
+  double w_final;
+  double A_final[TP_MAX_PARAMS];
+  int nscat, nevents, end, pad;
+} tp_record;
+
+/* One batch of histories.  n_histories[n_instances] (host array) histories per
+ * instance with ids first_history[i] .. first_history[i]+n_histories[i]-1
+ * (first_history may be NULL: 0).  Random numbers are Philox4x32-10 keyed by
+ * (seed, event, sub-stream, history id, instance), so results do not depend on
+ * the launch shape and runs over disjoint id ranges add up.
+ * want_grad accumulates the score-function tallies for tp_backward.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * block_size / ctas_per_sm: 0 = autotuned per scene.
+ * records: device array of n_records tp_record, or NULL. */
+typedef struct {
+  uint64_t seed;
+  const uint64_t* n_histories;
+  const uint64_t* first_history;
+  int want_grad;
+  void* stream;
+  int block_size;
+  int ctas_per_sm;
+  tp_record* records;
+  uint64_t n_records;
+} tp_run;
+
+/* Runs histories and accumulates their scores into the scene's tallies
+ * (sum w, sum w^2 per bin per instance, and the gradient tallies).  Returns
+ * after the launch is queued on the stream; the per-run status (truncation
+ * count, lost particles) is available from tp_get_counters. */
+tp_status tp_run_histories(tp_scene* s, const tp_run* r);
+
+/* Mean and standard error per source history of every bin of `tally` for
+ * `instance`: mean = sum w / N, stderr = sqrt((sum w^2/N - mean^2)/(N-1)),
+ * N = histories run for that instance.  mean / stderr_ receive nbins[0]*nbins[1]
+ * doubles (device pointers if on_device, else host; the call then
+ * synchronises).  stderr_ may be NULL. */
+tp_status tp_read_tallies(tp_scene* s, int tally, int instance, double* mean, double* stderr_,
+                          int on_device);
+
+/* Raw accumulators of one instance: sum w and sum w^2 over every bin of every
+ * tally (concatenated in tally order); J and J2 (may be NULL) receive
+ * [n_params][total bins] of sum w A_p and sum (w A_p)^2. */
+tp_status tp_read_raw(tp_scene* s, int instance, double* sum, double* sumsq, double* J, double* J2,
+                      int on_device);
+
+/* Backward pass of the tallies with respect to the instance parameters:
+ *   grad_params[i][p] = sum_b grad_tallies[i][b] * dmean_b/dtheta_p
+ * over all bins b of all tallies of instance i, where dmean/dtheta comes from
+ * the score-function (likelihood-ratio) accumulators of the forward run (plus
+ * the interface term for radii).  grad_tallies: [n_instances][total bins];
+ * grad_params: [n_instances][n_params]; both on the device if on_device.
+ * The derivative is per unit of the parameter (radius: per cm; scale and
+ * density: per unit multiplier). */
+tp_status tp_backward(tp_scene* s, const double* grad_tallies, double* grad_params, int on_device,
+                      void* stream);
+
+/* Replaces the instance parameters ([n_instances][n_params], same layout as
+ * tp_scene_desc.inst_params) and re-validates the geometry (TP_ERR_GEOMETRY
+ * leaves the old values in place).  Tallies are not reset. */
+tp_status tp_set_params(tp_scene* s, const double* inst_params);
+
+/* Zeroes every tally and history count. */
+tp_status tp_reset_tallies(tp_scene* s);
+
+/* Counters since the last reset: histories, events, collisions, boundary
+ * crossings, truncated histories, lost neutrons, mirror reflections, derivative
+ * secondaries.  Synchronises. */
+tp_status tp_get_counters(tp_scene* s, int64_t out[8]);
+
+/* Launch configuration the autotuner picked (or the forced one): block size and
+ * CTAs per SM. */
+tp_status tp_get_launch(tp_scene* s, int* block_size, int* ctas_per_sm);
+
+/* Total bins over all tallies (per instance). */
+int tp_total_bins(const tp_scene* s);
+
+void tp_destroy_scene(tp_scene* s);
+const char* tp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

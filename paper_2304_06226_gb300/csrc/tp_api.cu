@@ -1,0 +1,818 @@
+// tp_api.cu -- host runtime behind the C ABI of include/tp.h: scene validation,
+// device tables, launch configuration, tallies, backward pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tp_internal.h"
+
+using namespace tp;
+
+namespace {
+
+thread_local std::string g_err;
+
+tp_status fail(tp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define TP_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+struct Mat {
+  tp_material m;
+  std::vector<double> d, mult, F2;  // sorted by d descending
+  double g[TP_NPROC] = {1.0, 1.0, 1.0};
+};
+
+}  // namespace
+
+struct tp_scene {
+  int device = 0;
+  int sm_count = 0;
+  int precision = TP_FP32;
+  int event_cap = 4096;
+  // description (owned copies)
+  int world_shape = TP_BOX;
+  double world_c[3] = {0, 0, 0}, world_p[3] = {0, 0, 0};
+  std::vector<tp_prim> prims;
+  std::vector<tp_mirror> mirrors;
+  tp_source source{};
+  std::vector<tp_tally_desc> tallies;
+  std::vector<int> tally_off;
+  int total_bins = 0;
+  int n_inst = 1, n_par = 0;
+  std::vector<double> inst_params;  // [n_inst][kMaxPar]
+  std::vector<int> param_kind;
+  double radius_nominal = 0.0;
+  std::vector<Mat> mats;
+  bool have_materials = false;
+  // device tables
+  uint8_t* d_blob = nullptr;
+  size_t blob_cap = 0;
+  uint32_t blob_bytes = 0;
+  uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_tallies = 0, off_line_d = 0, off_line_cum = 0;
+  bool blob_dirty = true;
+  // tallies
+  double *d_sum = nullptr, *d_sumsq = nullptr, *d_J = nullptr, *d_J2 = nullptr;
+  std::vector<double> n_done;  // histories run per instance
+  // per-run work description
+  unsigned long long *d_prefix = nullptr, *d_first = nullptr, *h_stage = nullptr;
+  double* d_params = nullptr;
+  double* d_aux = nullptr;  // backward: [n_inst][n_par] scale + [n_inst] n_done
+  double* h_aux = nullptr;
+  unsigned long long* d_work = nullptr;
+  unsigned long long* d_counters = nullptr;
+  int* d_status = nullptr;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
+  // launch configuration
+  int block = 0, ctas_per_sm = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Validation helpers
+// ---------------------------------------------------------------------------
+struct Box3 { double lo[3], hi[3]; };
+
+double bound_r0(const tp_scene* s, const tp_prim& p, int inst) {
+  double r = p.params[0];
+  if (p.bind_rmin) {
+    for (int i = 0; i < s->n_par; ++i)
+      if (s->param_kind[i] == TP_PAR_RADIUS) r += s->inst_params[(size_t)inst * kMaxPar + i] - s->radius_nominal;
+  }
+  return r;
+}
+double bound_r1(const tp_scene* s, const tp_prim& p, int inst) {
+  double r = p.params[1];
+  if (p.bind_rmax) {
+    for (int i = 0; i < s->n_par; ++i)
+      if (s->param_kind[i] == TP_PAR_RADIUS) r += s->inst_params[(size_t)inst * kMaxPar + i] - s->radius_nominal;
+  }
+  return r;
+}
+
+Box3 aabb(const tp_scene* s, const tp_prim& p, int inst) {
+  Box3 b;
+  double h[3];
+  if (p.shape == TP_BOX) {
+    for (int i = 0; i < 3; ++i) h[i] = p.params[i];
+  } else if (p.shape == TP_TUBE) {
+    const double r = bound_r1(s, p, inst);
+    for (int i = 0; i < 3; ++i) h[i] = r;
+    h[p.axis] = p.params[2];
+  } else {
+    const double r = bound_r1(s, p, inst);
+    for (int i = 0; i < 3; ++i) h[i] = r;
+  }
+  for (int i = 0; i < 3; ++i) { b.lo[i] = p.centre[i] - h[i]; b.hi[i] = p.centre[i] + h[i]; }
+  return b;
+}
+
+bool point_inside(const tp_scene* s, const tp_prim& p, int inst, const double x[3], double shrink) {
+  double d[3] = {x[0] - p.centre[0], x[1] - p.centre[1], x[2] - p.centre[2]};
+  if (p.shape == TP_BOX)
+    return std::fabs(d[0]) < p.params[0] - shrink && std::fabs(d[1]) < p.params[1] - shrink &&
+           std::fabs(d[2]) < p.params[2] - shrink;
+  const double r0 = bound_r0(s, p, inst), r1 = bound_r1(s, p, inst);
+  if (p.shape == TP_TUBE) {
+    double rho2 = 0;
+    for (int i = 0; i < 3; ++i)
+      if (i != p.axis) rho2 += d[i] * d[i];
+    const double rho = std::sqrt(rho2);
+    return rho > r0 + shrink && rho < r1 - shrink && std::fabs(d[p.axis]) < p.params[2] - shrink;
+  }
+  const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  return r > r0 + shrink && r < r1 - shrink;
+}
+
+// true if primitives a and b share interior volume (exact for boxes, coaxial
+// tubes and concentric spheres; otherwise a sampling test on a 9^3 grid)
+bool overlap(const tp_scene* s, const tp_prim& a, const tp_prim& b, int inst) {
+  const Box3 A = aabb(s, a, inst), B = aabb(s, b, inst);
+  for (int i = 0; i < 3; ++i)
+    if (A.hi[i] <= B.lo[i] || B.hi[i] <= A.lo[i]) return false;
+  if (a.shape == TP_BOX && b.shape == TP_BOX) return true;
+  const double eps = 1e-12;
+  if (a.shape == TP_TUBE && b.shape == TP_TUBE && a.axis == b.axis) {
+    bool coaxial = true;
+    for (int i = 0; i < 3; ++i)
+      if (i != a.axis && std::fabs(a.centre[i] - b.centre[i]) > eps) coaxial = false;
+    if (coaxial) {
+      const double ra0 = bound_r0(s, a, inst), ra1 = bound_r1(s, a, inst);
+      const double rb0 = bound_r0(s, b, inst), rb1 = bound_r1(s, b, inst);
+      return ra0 < rb1 - eps && rb0 < ra1 - eps;  // axial overlap already implied by the boxes
+    }
+  }
+  if (a.shape == TP_SPHERE && b.shape == TP_SPHERE) {
+    const double dx = a.centre[0] - b.centre[0], dy = a.centre[1] - b.centre[1], dz = a.centre[2] - b.centre[2];
+    const double dc = std::sqrt(dx * dx + dy * dy + dz * dz);
+    const double ra0 = bound_r0(s, a, inst), ra1 = bound_r1(s, a, inst);
+    const double rb0 = bound_r0(s, b, inst), rb1 = bound_r1(s, b, inst);
+    if (dc < eps) return ra0 < rb1 - eps && rb0 < ra1 - eps;
+    if (dc >= ra1 + rb1) return false;
+  }
+  // sampling test over the intersection of the two boxes
+  double lo[3], hi[3];
+  for (int i = 0; i < 3; ++i) { lo[i] = std::max(A.lo[i], B.lo[i]); hi[i] = std::min(A.hi[i], B.hi[i]); }
+  const int n = 9;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) {
+        const double x[3] = {lo[0] + (hi[0] - lo[0]) * (i + 0.5) / n, lo[1] + (hi[1] - lo[1]) * (j + 0.5) / n,
+                             lo[2] + (hi[2] - lo[2]) * (k + 0.5) / n};
+        if (point_inside(s, a, inst, x, 1e-9) && point_inside(s, b, inst, x, 1e-9)) return true;
+      }
+  return false;
+}
+
+bool inside_world(const tp_scene* s, const tp_prim& p, int inst) {
+  const Box3 b = aabb(s, p, inst);
+  if (s->world_shape == TP_BOX) {
+    for (int i = 0; i < 3; ++i)
+      if (b.lo[i] <= s->world_c[i] - s->world_p[i] || b.hi[i] >= s->world_c[i] + s->world_p[i]) return false;
+    return true;
+  }
+  double far2 = 0;
+  for (int i = 0; i < 3; ++i) {
+    const double e = std::max(std::fabs(b.lo[i] - s->world_c[i]), std::fabs(b.hi[i] - s->world_c[i]));
+    far2 += e * e;
+  }
+  return std::sqrt(far2) < s->world_p[1];
+}
+
+tp_status validate_geometry(tp_scene* s) {
+  const int np = (int)s->prims.size();
+  // insts to check: every instance when the radius moves and the scene is small
+  bool moving = false;
+  for (const auto& p : s->prims) moving |= (p.bind_rmin || p.bind_rmax);
+  const int ninst = (moving && np <= 64) ? s->n_inst : 1;
+  for (int q = 0; q < ninst; ++q) {
+    for (int i = 0; i < np; ++i) {
+      const tp_prim& p = s->prims[i];
+      if (p.shape != TP_BOX) {
+        const double r0 = bound_r0(s, p, q), r1 = bound_r1(s, p, q);
+        if (!(r0 >= 0.0) || !(r1 > r0))
+          return fail(TP_ERR_GEOMETRY, "primitive %d (instance %d): radii %g..%g invalid", i, q, r0, r1);
+      }
+      if (!inside_world(s, p, q)) return fail(TP_ERR_GEOMETRY, "primitive %d (instance %d) not inside the world", i, q);
+    }
+    // pairwise: bounding-sphere rejection first
+    std::vector<double> bc(3 * (size_t)np), br(np);
+    for (int i = 0; i < np; ++i) {
+      const Box3 b = aabb(s, s->prims[i], q);
+      double r2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        bc[3 * i + k] = 0.5 * (b.lo[k] + b.hi[k]);
+        const double h = 0.5 * (b.hi[k] - b.lo[k]);
+        r2 += h * h;
+      }
+      br[i] = std::sqrt(r2);
+    }
+    for (int i = 0; i < np; ++i)
+      for (int j = i + 1; j < np; ++j) {
+        const double dx = bc[3 * i] - bc[3 * j], dy = bc[3 * i + 1] - bc[3 * j + 1], dz = bc[3 * i + 2] - bc[3 * j + 2];
+        if (dx * dx + dy * dy + dz * dz >= (br[i] + br[j]) * (br[i] + br[j])) continue;
+        if (overlap(s, s->prims[i], s->prims[j], q))
+          return fail(TP_ERR_GEOMETRY, "primitives %d and %d overlap (instance %d)", i, j, q);
+      }
+  }
+  return TP_OK;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// ---------------------------------------------------------------------------
+// Device scene tables in precision R
+// ---------------------------------------------------------------------------
+template <typename R>
+std::vector<uint8_t> build_blob(tp_scene* s) {
+  const int np = (int)s->prims.size(), nm = (int)s->mats.size(), nmir = (int)s->mirrors.size(),
+            nt = (int)s->tallies.size();
+  int nl = 0;
+  for (const auto& m : s->mats) nl += (int)m.d.size();
+  size_t off = 0;
+  s->off_prims = (uint32_t)off; off = align16(off + sizeof(DPrim<R>) * np);
+  s->off_mats = (uint32_t)off; off = align16(off + sizeof(DMat<R>) * std::max(nm, 1));
+  s->off_mirrors = (uint32_t)off; off = align16(off + sizeof(DMirror<R>) * std::max(nmir, 1));
+  s->off_tallies = (uint32_t)off; off = align16(off + sizeof(DTally<R>) * std::max(nt, 1));
+  s->off_line_d = (uint32_t)off; off = align16(off + sizeof(R) * std::max(nl, 1));
+  s->off_line_cum = (uint32_t)off; off = align16(off + sizeof(R) * (nl + std::max(nm, 1)));
+  std::vector<uint8_t> blob(off, 0);
+  auto* P = reinterpret_cast<DPrim<R>*>(blob.data() + s->off_prims);
+  for (int i = 0; i < np; ++i) {
+    const tp_prim& p = s->prims[i];
+    DPrim<R> d{};
+    for (int k = 0; k < 3; ++k) { d.c[k] = (R)p.centre[k]; d.p[k] = (R)p.params[k]; }
+    d.shape = p.shape; d.axis = p.axis; d.material = p.material; d.role = p.role;
+    d.mirror = p.mirror; d.flags = (p.bind_rmin ? F_BIND_RMIN : 0) | (p.bind_rmax ? F_BIND_RMAX : 0);
+    d.entry_mask = 0; d.exit_mask = 0;
+    for (int t = 0; t < nt; ++t) {
+      if (s->tallies[t].volume != i) continue;
+      if (s->tallies[t].trigger == TP_PTS_ENTRY) d.entry_mask |= 1 << t;
+      else d.exit_mask |= 1 << t;
+    }
+    P[i] = d;
+  }
+  auto* M = reinterpret_cast<DMat<R>*>(blob.data() + s->off_mats);
+  auto* LD = reinterpret_cast<R*>(blob.data() + s->off_line_d);
+  auto* LC = reinterpret_cast<R*>(blob.data() + s->off_line_cum);
+  int lo = 0;
+  for (int i = 0; i < nm; ++i) {
+    const Mat& m = s->mats[i];
+    DMat<R> d{};
+    d.sig_abs_ref = (R)m.m.sigma_abs_ref;
+    d.sig_inc = (R)m.m.sigma_inc;
+    d.bragg_pref = m.d.empty() ? R(0) : (R)(1.0 / (2.0 * m.m.V0 * m.m.V0));
+    for (int k = 0; k < TP_NPROC; ++k) d.g[k] = (R)m.g[k];
+    d.abs_1v = m.m.abs_1v;
+    d.nlines = (int)m.d.size();
+    d.line_off = lo;
+    d.cum_off = lo + i;
+    d.density_par = m.m.density_param;
+    d.scale_par = m.m.scale_param;
+    double acc = 0.0;
+    LC[d.cum_off] = R(0);
+    for (int k = 0; k < d.nlines; ++k) {
+      LD[lo + k] = (R)m.d[k];
+      acc += m.mult[k] * m.F2[k] * m.d[k];
+      LC[d.cum_off + k + 1] = (R)acc;
+    }
+    lo += d.nlines;
+    M[i] = d;
+  }
+  auto* MI = reinterpret_cast<DMirror<R>*>(blob.data() + s->off_mirrors);
+  for (int i = 0; i < nmir; ++i) {
+    const tp_mirror& m = s->mirrors[i];
+    MI[i] = DMirror<R>{(R)m.m, (R)m.R0, (R)m.Qc, (R)m.alpha, (R)m.W, (R)(m.m * m.Qc), R(0), R(0)};
+  }
+  auto* T = reinterpret_cast<DTally<R>*>(blob.data() + s->off_tallies);
+  for (int t = 0; t < nt; ++t) {
+    const tp_tally_desc& d = s->tallies[t];
+    DTally<R> x{};
+    for (int k = 0; k < 2; ++k) {
+      x.lo[k] = (R)d.lo[k];
+      x.hi[k] = (R)d.hi[k];
+      x.inv_w[k] = (R)(d.nbins[k] / (d.hi[k] - d.lo[k]));
+    }
+    double an = std::sqrt(d.axis[0] * d.axis[0] + d.axis[1] * d.axis[1] + d.axis[2] * d.axis[2]);
+    if (!(an > 0)) an = 1.0;
+    for (int k = 0; k < 3; ++k) { x.origin[k] = (R)d.origin[k]; x.axis[k] = (R)(d.axis[k] / an); }
+    x.kind = d.kind; x.trigger = d.trigger; x.volume = d.volume; x.face = d.face; x.scat = d.scat;
+    x.nb0 = d.nbins[0]; x.nb1 = d.nbins[1]; x.offset = s->tally_off[t];
+    T[t] = x;
+  }
+  return blob;
+}
+
+tp_status upload_blob(tp_scene* s) {
+  std::vector<uint8_t> blob = s->precision == TP_FP64 ? build_blob<double>(s) : build_blob<float>(s);
+  if (blob.size() > s->blob_cap) {
+    if (s->d_blob) cudaFree(s->d_blob);
+    s->d_blob = nullptr;
+    TP_CUDA(cudaMalloc(&s->d_blob, blob.size()));
+    s->blob_cap = blob.size();
+  }
+  TP_CUDA(cudaMemcpy(s->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  s->blob_bytes = (uint32_t)blob.size();
+  s->blob_dirty = false;
+  return TP_OK;
+}
+
+constexpr uint32_t kMaxStagedBlob = 96 * 1024;  // larger tables are read through L1/L2
+
+template <typename R>
+void fill_common(const tp_scene* s, KParams<R>& k) {
+  k.blob = s->d_blob;
+  k.blob_bytes = s->blob_bytes;
+  k.off_prims = s->off_prims; k.off_mats = s->off_mats; k.off_mirrors = s->off_mirrors;
+  k.off_tallies = s->off_tallies; k.off_line_d = s->off_line_d; k.off_line_cum = s->off_line_cum;
+  k.stage_blob = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
+  k.nprim = (int)s->prims.size();
+  k.nmat = (int)s->mats.size();
+  k.ntally = (int)s->tallies.size();
+  k.npar = s->n_par;
+  k.radius_par = -1;
+  for (int i = 0; i < kMaxPar; ++i) k.param_kind[i] = i < s->n_par ? s->param_kind[i] : -1;
+  for (int i = 0; i < s->n_par; ++i)
+    if (s->param_kind[i] == TP_PAR_RADIUS) k.radius_par = i;
+  k.radius_nominal = (R)s->radius_nominal;
+  k.world_shape = s->world_shape;
+  for (int i = 0; i < 3; ++i) { k.world_c[i] = (R)s->world_c[i]; k.world_p[i] = (R)s->world_p[i]; }
+  k.world_entry_mask = 0;
+  k.world_exit_mask = 0;
+  for (int t = 0; t < (int)s->tallies.size(); ++t)
+    if (s->tallies[t].volume == -1) {
+      if (s->tallies[t].trigger == TP_PTS_EXIT) k.world_exit_mask |= 1 << t;
+      else k.world_entry_mask |= 1 << t;
+    }
+  const tp_source& src = s->source;
+  k.src_kind = src.kind;
+  k.src_aperture = src.has_aperture;
+  for (int i = 0; i < 3; ++i) k.src_c[i] = (R)src.centre[i];
+  for (int i = 0; i < 2; ++i) {
+    k.src_half[i] = (R)src.half[i];
+    k.src_div[i] = (R)src.div[i];
+    k.src_ap[i] = (R)src.aperture[i];
+  }
+  k.src_lam_lo = (R)src.lambda_lo;
+  k.src_lam_hi = (R)src.lambda_hi;
+  k.event_cap = s->event_cap;
+  k.n_inst = s->n_inst;
+  k.inst_prefix = s->d_prefix;
+  k.inst_first = s->d_first;
+  k.inst_params = s->d_params;
+  k.work_counter = s->d_work;
+  k.sum = s->d_sum; k.sumsq = s->d_sumsq; k.J = s->d_J; k.J2 = s->d_J2;
+  k.total_bins = s->total_bins;
+  k.counters = s->d_counters;
+  k.status = s->d_status;
+}
+
+size_t smem_bytes(const tp_scene* s) { return s->blob_bytes <= kMaxStagedBlob ? align16(s->blob_bytes) : 0; }
+
+tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* block, int* ctas) {
+  int b = req_block > 0 ? req_block : (s->block > 0 ? s->block : 256);
+  if (b % 32 != 0 || b < 32 || b > 512) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 512]", b);
+  int occ = 0;
+  TP_CUDA(occupancy_transport(s->precision, grad, b, smem_bytes(s), &occ));
+  if (occ < 1) return fail(TP_ERR_INVALID_ARG, "block_size %d does not fit on an SM", b);
+  int c = req_ctas > 0 ? std::min(req_ctas, occ) : occ;
+  *block = b;
+  *ctas = c;
+  return TP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* tp_last_error(void) { return g_err.c_str(); }
+
+int tp_total_bins(const tp_scene* s) { return s ? s->total_bins : 0; }
+
+tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
+  g_err.clear();
+  if (!d || !out) return fail(TP_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (d->precision != TP_FP32 && d->precision != TP_FP64) return fail(TP_ERR_INVALID_ARG, "precision %d", d->precision);
+  if (d->world_shape != TP_BOX && d->world_shape != TP_SPHERE) return fail(TP_ERR_INVALID_ARG, "world shape %d", d->world_shape);
+  if (!finite_all(d->world_centre, 3) || !finite_all(d->world_params, 3)) return fail(TP_ERR_INVALID_ARG, "world not finite");
+  if (d->world_shape == TP_BOX && !(d->world_params[0] > 0 && d->world_params[1] > 0 && d->world_params[2] > 0))
+    return fail(TP_ERR_INVALID_ARG, "world half extents must be positive");
+  if (d->world_shape == TP_SPHERE && !(d->world_params[1] > 0)) return fail(TP_ERR_INVALID_ARG, "world radius must be positive");
+  if (d->n_prims < 0 || (d->n_prims > 0 && !d->prims)) return fail(TP_ERR_INVALID_ARG, "prims");
+  if (d->n_mirrors < 0 || (d->n_mirrors > 0 && !d->mirrors)) return fail(TP_ERR_INVALID_ARG, "mirrors");
+  if (d->n_tallies < 0 || d->n_tallies > TP_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))
+    return fail(TP_ERR_INVALID_ARG, "n_tallies %d (max %d)", d->n_tallies, TP_MAX_TALLIES);
+  if (d->n_instances < 1) return fail(TP_ERR_INVALID_ARG, "n_instances must be >= 1");
+  if (d->n_params < 0 || d->n_params > TP_MAX_PARAMS) return fail(TP_ERR_INVALID_ARG, "n_params %d (max %d)", d->n_params, TP_MAX_PARAMS);
+  if (d->n_params > 0 && (!d->inst_params || !d->param_kind)) return fail(TP_ERR_INVALID_ARG, "inst_params / param_kind");
+  if (d->event_cap < 0) return fail(TP_ERR_INVALID_ARG, "event_cap");
+
+  tp_scene* s = new tp_scene();
+  auto bail = [&](tp_status st) { tp_destroy_scene(s); return st; };
+  s->precision = d->precision;
+  s->event_cap = d->event_cap > 0 ? d->event_cap : 4096;
+  s->world_shape = d->world_shape;
+  for (int i = 0; i < 3; ++i) { s->world_c[i] = d->world_centre[i]; s->world_p[i] = d->world_params[i]; }
+  s->prims.assign(d->prims, d->prims + d->n_prims);
+  s->mirrors.assign(d->mirrors, d->mirrors + d->n_mirrors);
+  s->source = d->source;
+  s->tallies.assign(d->tallies, d->tallies + d->n_tallies);
+  s->n_inst = d->n_instances;
+  s->n_par = d->n_params;
+  s->param_kind.assign(d->param_kind, d->param_kind + d->n_params);
+  s->radius_nominal = d->radius_nominal;
+  s->inst_params.assign((size_t)s->n_inst * kMaxPar, 0.0);
+  int n_radius = 0;
+  for (int p = 0; p < s->n_par; ++p) {
+    if (s->param_kind[p] < TP_PAR_RADIUS || s->param_kind[p] > TP_PAR_DENSITY) return bail(fail(TP_ERR_INVALID_ARG, "param_kind[%d]", p));
+    n_radius += s->param_kind[p] == TP_PAR_RADIUS;
+  }
+  if (n_radius > 1) return bail(fail(TP_ERR_INVALID_ARG, "at most one radius parameter"));
+  for (int q = 0; q < s->n_inst; ++q)
+    for (int p = 0; p < s->n_par; ++p) {
+      const double v = d->inst_params[(size_t)q * s->n_par + p];
+      if (!std::isfinite(v)) return bail(fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] not finite", q, p));
+      if (s->param_kind[p] != TP_PAR_RADIUS && !(v > 0)) return bail(fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] must be > 0", q, p));
+      s->inst_params[(size_t)q * kMaxPar + p] = v;
+    }
+  // primitives
+  for (int i = 0; i < d->n_prims; ++i) {
+    const tp_prim& p = s->prims[i];
+    if (p.shape < TP_BOX || p.shape > TP_SPHERE) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: shape %d", i, p.shape));
+    if (p.axis < 0 || p.axis > 2) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: axis %d", i, p.axis));
+    if (p.role < TP_ROLE_BULK || p.role > TP_ROLE_BLACK) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: role %d", i, p.role));
+    if (p.mirror < -1 || p.mirror >= d->n_mirrors) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: mirror %d", i, p.mirror));
+    if (p.material < -1) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: material %d", i, p.material));
+    if (!finite_all(p.centre, 3) || !finite_all(p.params, 3)) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: not finite", i));
+    if (p.shape == TP_BOX && !(p.params[0] > 0 && p.params[1] > 0 && p.params[2] > 0))
+      return bail(fail(TP_ERR_INVALID_ARG, "prim %d: box half extents must be positive", i));
+    if (p.shape == TP_TUBE && !(p.params[2] > 0)) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: tube half height", i));
+    if ((p.bind_rmin || p.bind_rmax) && (p.shape == TP_BOX || n_radius == 0))
+      return bail(fail(TP_ERR_INVALID_ARG, "prim %d: radius binding needs a tube/sphere and a radius parameter", i));
+  }
+  for (int i = 0; i < d->n_mirrors; ++i) {
+    const tp_mirror& m = s->mirrors[i];
+    if (!(m.R0 >= 0 && m.Qc >= 0 && m.W > 0 && m.alpha >= 0 && m.m >= 0) ||
+        !finite_all(&m.m, 1) || !finite_all(&m.R0, 1))
+      return bail(fail(TP_ERR_INVALID_ARG, "mirror %d: need R0, Qc, alpha, m >= 0 and W > 0", i));
+  }
+  // source
+  const tp_source& src = s->source;
+  if (src.kind != TP_SRC_PENCIL && src.kind != TP_SRC_RECT) return bail(fail(TP_ERR_INVALID_ARG, "source kind %d", src.kind));
+  if (!(src.lambda_lo > 0) || !(src.lambda_hi >= src.lambda_lo) || !std::isfinite(src.lambda_hi))
+    return bail(fail(TP_ERR_INVALID_ARG, "source wavelength range"));
+  if (!(src.div[0] >= 0 && src.div[0] < 1.5 && src.div[1] >= 0 && src.div[1] < 1.5))
+    return bail(fail(TP_ERR_INVALID_ARG, "source divergence must be in [0, 1.5) rad"));
+  // tallies
+  s->tally_off.resize(s->tallies.size() + 1);
+  long long tb = 0;
+  for (int t = 0; t < d->n_tallies; ++t) {
+    const tp_tally_desc& T = s->tallies[t];
+    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_WLX) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: kind", t));
+    if (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: trigger", t));
+    if (T.volume < -1 || T.volume >= d->n_prims) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: volume %d", t, T.volume));
+    if (T.volume == -1 && T.trigger == TP_PTS_ENTRY) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: the world has no ENTRY", t));
+    if (T.nbins[0] < 1 || T.nbins[1] < 1) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: bins", t));
+    if (T.kind == TP_TALLY_COUNT && (T.nbins[0] != 1 || T.nbins[1] != 1)) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: a count has one bin", t));
+    if (T.kind == TP_TALLY_ANGULAR && T.nbins[1] != 1) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: angular is 1-D", t));
+    const int dims = (T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) ? 2 : (T.kind == TP_TALLY_ANGULAR ? 1 : 0);
+    for (int k = 0; k < dims; ++k)
+      if (!(T.hi[k] > T.lo[k]) || !std::isfinite(T.hi[k]) || !std::isfinite(T.lo[k]))
+        return bail(fail(TP_ERR_INVALID_ARG, "tally %d: range of axis %d", t, k));
+    s->tally_off[t] = (int)tb;
+    tb += (long long)T.nbins[0] * T.nbins[1];
+  }
+  if (tb > (1ll << 30)) return bail(fail(TP_ERR_INVALID_ARG, "too many bins"));
+  s->total_bins = (int)tb;
+  s->tally_off[s->tallies.size()] = (int)tb;
+  tp_status st = validate_geometry(s);
+  if (st != TP_OK) return bail(st);
+  // device
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (e != cudaSuccess) return bail(fail(TP_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+  const size_t nb = (size_t)s->n_inst * std::max(1, s->total_bins);
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    cudaError_t r = cudaMalloc(p, bytes);
+    if (r != cudaSuccess) { fail(r == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(r)); return false; }
+    return true;
+  };
+  if (!alloc((void**)&s->d_sum, nb * sizeof(double)) || !alloc((void**)&s->d_sumsq, nb * sizeof(double)))
+    return bail(TP_ERR_OOM);
+  if (s->n_par > 0) {
+    if (!alloc((void**)&s->d_J, nb * s->n_par * sizeof(double)) || !alloc((void**)&s->d_J2, nb * s->n_par * sizeof(double)))
+      return bail(TP_ERR_OOM);
+  }
+  if (!alloc((void**)&s->d_prefix, (s->n_inst + 1) * sizeof(unsigned long long)) ||
+      !alloc((void**)&s->d_first, s->n_inst * sizeof(unsigned long long)) ||
+      !alloc((void**)&s->d_params, (size_t)s->n_inst * kMaxPar * sizeof(double)) ||
+      !alloc((void**)&s->d_aux, ((size_t)s->n_inst * (kMaxPar + 1)) * sizeof(double)) ||
+      !alloc((void**)&s->d_work, sizeof(unsigned long long)) ||
+      !alloc((void**)&s->d_counters, kNumCounters * sizeof(unsigned long long)) ||
+      !alloc((void**)&s->d_status, sizeof(int)))
+    return bail(TP_ERR_OOM);
+  if (cudaMallocHost((void**)&s->h_stage, (2 * (size_t)s->n_inst + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->h_aux, ((size_t)s->n_inst * (kMaxPar + 1)) * sizeof(double)) != cudaSuccess)
+    return bail(fail(TP_ERR_OOM, "pinned staging buffers"));
+  if (cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(TP_ERR_CUDA, "event"));
+  if (cudaMemcpy(s->d_params, s->inst_params.data(), s->inst_params.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(TP_ERR_CUDA, "upload instance parameters"));
+  s->n_done.assign(s->n_inst, 0.0);
+  st = tp_reset_tallies(s);
+  if (st != TP_OK) return bail(st);
+  *out = s;
+  return TP_OK;
+}
+
+tp_status tp_set_materials(tp_scene* s, const tp_material* m, int n) {
+  g_err.clear();
+  if (!s || (n > 0 && !m) || n < 0) return fail(TP_ERR_INVALID_ARG, "null argument");
+  std::vector<Mat> mats(n);
+  for (int i = 0; i < n; ++i) {
+    const tp_material& x = m[i];
+    if (!(x.sigma_abs_ref >= 0) || !(x.sigma_inc >= 0) || !std::isfinite(x.sigma_abs_ref) || !std::isfinite(x.sigma_inc))
+      return fail(TP_ERR_INVALID_ARG, "material %d: cross sections must be finite and >= 0", i);
+    if (x.n_lines < 0 || (x.n_lines > 0 && (!x.d || !x.mult || !x.F2)))
+      return fail(TP_ERR_INVALID_ARG, "material %d: Bragg line arrays", i);
+    if (x.n_lines > 0 && !(x.V0 > 0)) return fail(TP_ERR_INVALID_ARG, "material %d: V0 must be > 0", i);
+    for (int k = 0; k < x.n_lines; ++k)
+      if (!(x.d[k] > 0) || !(x.mult[k] >= 0) || !(x.F2[k] >= 0) || !std::isfinite(x.d[k]) || !std::isfinite(x.F2[k]))
+        return fail(TP_ERR_INVALID_ARG, "material %d line %d: need d > 0, mult >= 0, F2 >= 0", i, k);
+    for (int which = 0; which < 2; ++which) {
+      const int p = which ? x.scale_param : x.density_param;
+      if (p < -1 || p >= s->n_par) return fail(TP_ERR_INVALID_ARG, "material %d: parameter index %d", i, p);
+      if (p >= 0 && s->param_kind[p] != (which ? TP_PAR_SCALE : TP_PAR_DENSITY))
+        return fail(TP_ERR_INVALID_ARG, "material %d: parameter %d has the wrong kind", i, p);
+    }
+    mats[i].m = x;
+    std::vector<int> idx(x.n_lines);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return x.d[a] > x.d[b]; });
+    for (int k : idx) { mats[i].d.push_back(x.d[k]); mats[i].mult.push_back(x.mult[k]); mats[i].F2.push_back(x.F2[k]); }
+    mats[i].m.d = mats[i].m.mult = mats[i].m.F2 = nullptr;
+  }
+  for (size_t i = 0; i < s->prims.size(); ++i)
+    if (s->prims[i].material >= n) return fail(TP_ERR_INVALID_ARG, "prim %zu uses material %d of %d", i, s->prims[i].material, n);
+  s->mats = std::move(mats);
+  s->have_materials = true;
+  s->blob_dirty = true;
+  return TP_OK;
+}
+
+tp_status tp_set_bias(tp_scene* s, int material, const double g[TP_NPROC]) {
+  g_err.clear();
+  if (!s || !g) return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (!s->have_materials) return fail(TP_ERR_STATE, "tp_set_materials first");
+  if (material < 0 || material >= (int)s->mats.size()) return fail(TP_ERR_INVALID_ARG, "material %d", material);
+  for (int i = 0; i < TP_NPROC; ++i)
+    if (!(g[i] >= 0) || !std::isfinite(g[i])) return fail(TP_ERR_INVALID_ARG, "bias factor %d must be finite and >= 0", i);
+  for (int i = 0; i < TP_NPROC; ++i) s->mats[material].g[i] = g[i];
+  s->blob_dirty = true;
+  return TP_OK;
+}
+
+tp_status tp_set_params(tp_scene* s, const double* inst_params) {
+  g_err.clear();
+  if (!s || (!inst_params && s->n_par > 0)) return fail(TP_ERR_INVALID_ARG, "null argument");
+  std::vector<double> old = s->inst_params;
+  for (int q = 0; q < s->n_inst; ++q)
+    for (int p = 0; p < s->n_par; ++p) {
+      const double v = inst_params[(size_t)q * s->n_par + p];
+      if (!std::isfinite(v) || (s->param_kind[p] != TP_PAR_RADIUS && !(v > 0))) {
+        s->inst_params = old;
+        return fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] = %g", q, p, v);
+      }
+      s->inst_params[(size_t)q * kMaxPar + p] = v;
+    }
+  tp_status st = validate_geometry(s);
+  if (st != TP_OK) {
+    s->inst_params = old;
+    return st;
+  }
+  TP_CUDA(cudaDeviceSynchronize());
+  TP_CUDA(cudaMemcpy(s->d_params, s->inst_params.data(), s->inst_params.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return TP_OK;
+}
+
+tp_status tp_reset_tallies(tp_scene* s) {
+  if (!s) return fail(TP_ERR_INVALID_ARG, "null scene");
+  const size_t nb = (size_t)s->n_inst * std::max(1, s->total_bins);
+  TP_CUDA(cudaMemset(s->d_sum, 0, nb * sizeof(double)));
+  TP_CUDA(cudaMemset(s->d_sumsq, 0, nb * sizeof(double)));
+  if (s->d_J) {
+    TP_CUDA(cudaMemset(s->d_J, 0, nb * s->n_par * sizeof(double)));
+    TP_CUDA(cudaMemset(s->d_J2, 0, nb * s->n_par * sizeof(double)));
+  }
+  TP_CUDA(cudaMemset(s->d_counters, 0, kNumCounters * sizeof(unsigned long long)));
+  TP_CUDA(cudaMemset(s->d_status, 0, sizeof(int)));
+  std::fill(s->n_done.begin(), s->n_done.end(), 0.0);
+  return TP_OK;
+}
+
+tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
+  g_err.clear();
+  if (!s || !r || !r->n_histories) return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (!s->have_materials) return fail(TP_ERR_STATE, "tp_set_materials first");
+  if (r->want_grad && s->n_par == 0) return fail(TP_ERR_INVALID_ARG, "want_grad without parameters");
+  if (r->records && s->precision != TP_FP64 && r->n_records > 0) { /* allowed in FP32 too */ }
+  cudaStream_t st = (cudaStream_t)r->stream;
+  if (s->blob_dirty) {
+    tp_status e = upload_blob(s);
+    if (e != TP_OK) return e;
+  }
+  // work description
+  if (s->stage_pending) {
+    TP_CUDA(cudaEventSynchronize(s->stage_done));
+    s->stage_pending = false;
+  }
+  unsigned long long total = 0;
+  for (int i = 0; i < s->n_inst; ++i) {
+    const unsigned long long first = r->first_history ? r->first_history[i] : 0ull;
+    if (r->n_histories[i] > 0xffffffffull || first + r->n_histories[i] > 0x100000000ull)
+      return fail(TP_ERR_INVALID_ARG, "instance %d: history ids must stay below 2^32", i);
+    s->h_stage[i] = total;
+    s->h_stage[s->n_inst + 1 + i] = first;
+    total += r->n_histories[i];
+  }
+  s->h_stage[s->n_inst] = total;
+  if (total == 0) return TP_OK;
+  int block = 0, ctas = 0;
+  tp_status e = pick_launch(s, r->want_grad != 0, r->block_size, r->ctas_per_sm, &block, &ctas);
+  if (e != TP_OK) return e;
+  TP_CUDA(cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+  TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+  TP_CUDA(cudaEventRecord(s->stage_done, st));
+  s->stage_pending = true;
+  TP_CUDA(cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st));
+  const int grid = s->sm_count * ctas;
+  const long long warps = (long long)grid * (block / 32);
+  long long chunk = (long long)(total / (unsigned long long)(warps * 8));
+  chunk = std::max(1ll, std::min(256ll, chunk));
+  const size_t smem = smem_bytes(s);
+  cudaError_t ce;
+  if (s->precision == TP_FP64) {
+    KParams<double> k{};
+    fill_common(s, k);
+    k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
+    k.total = total; k.chunk = (int)chunk;
+    k.records = r->records; k.n_records = r->records ? r->n_records : 0;
+    ce = launch_transport_f64(k, r->want_grad != 0, grid, block, smem, st);
+  } else {
+    KParams<float> k{};
+    fill_common(s, k);
+    k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
+    k.total = total; k.chunk = (int)chunk;
+    k.records = r->records; k.n_records = r->records ? r->n_records : 0;
+    ce = launch_transport_f32(k, r->want_grad != 0, grid, block, smem, st);
+  }
+  if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
+  for (int i = 0; i < s->n_inst; ++i) s->n_done[i] += (double)r->n_histories[i];
+  s->block = block;
+  s->ctas_per_sm = ctas;
+  return TP_OK;
+}
+
+tp_status tp_read_tallies(tp_scene* s, int tally, int instance, double* mean, double* err, int on_device) {
+  g_err.clear();
+  if (!s || !mean) return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (tally < 0 || tally >= (int)s->tallies.size()) return fail(TP_ERR_INVALID_ARG, "tally %d", tally);
+  if (instance < 0 || instance >= s->n_inst) return fail(TP_ERR_INVALID_ARG, "instance %d", instance);
+  const int nb = s->tallies[tally].nbins[0] * s->tallies[tally].nbins[1];
+  const size_t off = (size_t)instance * s->total_bins + s->tally_off[tally];
+  const double n = s->n_done[instance];
+  if (on_device) {
+    TP_CUDA(launch_stats(s->d_sum + off, s->d_sumsq + off, n, nb, mean, err, 0));
+    return TP_OK;
+  }
+  double *dm = nullptr, *de = nullptr;
+  TP_CUDA(cudaMalloc(&dm, 2 * (size_t)nb * sizeof(double)));
+  de = dm + nb;
+  cudaError_t e = launch_stats(s->d_sum + off, s->d_sumsq + off, n, nb, dm, de, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(mean, dm, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && err) e = cudaMemcpy(err, de, nb * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dm);
+  if (e != cudaSuccess) return fail(TP_ERR_CUDA, "read tallies: %s", cudaGetErrorString(e));
+  return TP_OK;
+}
+
+tp_status tp_read_raw(tp_scene* s, int instance, double* sum, double* sumsq, double* J, double* J2, int on_device) {
+  g_err.clear();
+  if (!s) return fail(TP_ERR_INVALID_ARG, "null scene");
+  if (instance < 0 || instance >= s->n_inst) return fail(TP_ERR_INVALID_ARG, "instance %d", instance);
+  const size_t nb = (size_t)s->total_bins;
+  const size_t off = (size_t)instance * nb;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  TP_CUDA(cudaDeviceSynchronize());
+  if (sum) TP_CUDA(cudaMemcpy(sum, s->d_sum + off, nb * sizeof(double), kind));
+  if (sumsq) TP_CUDA(cudaMemcpy(sumsq, s->d_sumsq + off, nb * sizeof(double), kind));
+  for (int p = 0; p < s->n_par; ++p) {
+    const size_t src = ((size_t)p * s->n_inst + instance) * nb;
+    if (J) TP_CUDA(cudaMemcpy(J + p * nb, s->d_J + src, nb * sizeof(double), kind));
+    if (J2) TP_CUDA(cudaMemcpy(J2 + p * nb, s->d_J2 + src, nb * sizeof(double), kind));
+  }
+  return TP_OK;
+}
+
+tp_status tp_backward(tp_scene* s, const double* grad_tallies, double* grad_params, int on_device, void* stream) {
+  g_err.clear();
+  if (!s || !grad_tallies || !grad_params) return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (s->n_par == 0 || !s->d_J) return fail(TP_ERR_STATE, "scene has no parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ni = s->n_inst, np = s->n_par;
+  // d/dtheta: radius per cm; scale and density are log-parameters in the
+  // accumulators, divided by the parameter value here
+  TP_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < ni; ++i) {
+    for (int p = 0; p < np; ++p) {
+      const double v = s->inst_params[(size_t)i * kMaxPar + p];
+      s->h_aux[(size_t)i * np + p] = s->param_kind[p] == TP_PAR_RADIUS ? 1.0 : 1.0 / v;
+    }
+    s->h_aux[(size_t)ni * np + i] = s->n_done[i];
+  }
+  TP_CUDA(cudaMemcpyAsync(s->d_aux, s->h_aux, ((size_t)ni * np + ni) * sizeof(double), cudaMemcpyHostToDevice, st));
+  const size_t gt_bytes = (size_t)ni * s->total_bins * sizeof(double);
+  const size_t gp_bytes = (size_t)ni * np * sizeof(double);
+  const double* d_gt = grad_tallies;
+  double* d_gp = grad_params;
+  double* tmp = nullptr;
+  if (!on_device) {
+    TP_CUDA(cudaMalloc(&tmp, gt_bytes + gp_bytes));
+    TP_CUDA(cudaMemcpyAsync(tmp, grad_tallies, gt_bytes, cudaMemcpyHostToDevice, st));
+    d_gt = tmp;
+    d_gp = tmp + (size_t)ni * s->total_bins;
+  }
+  cudaError_t e = launch_backward(s->d_J, d_gt, s->d_aux, s->d_aux + (size_t)ni * np, ni, np, s->total_bins, d_gp, st);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(grad_params, d_gp, gp_bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(TP_ERR_CUDA, "backward: %s", cudaGetErrorString(e));
+  return TP_OK;
+}
+
+tp_status tp_get_counters(tp_scene* s, int64_t out[8]) {
+  g_err.clear();
+  if (!s || !out) return fail(TP_ERR_INVALID_ARG, "null argument");
+  unsigned long long h[kNumCounters];
+  int status = 0;
+  TP_CUDA(cudaDeviceSynchronize());
+  TP_CUDA(cudaMemcpy(h, s->d_counters, sizeof h, cudaMemcpyDeviceToHost));
+  TP_CUDA(cudaMemcpy(&status, s->d_status, sizeof status, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < kNumCounters; ++i) out[i] = (int64_t)h[i];
+  if (status != 0) return fail((tp_status)status, "a device-side wait gave up (status %d)", status);
+  return TP_OK;
+}
+
+tp_status tp_get_launch(tp_scene* s, int* block, int* ctas) {
+  if (!s || !block || !ctas) return fail(TP_ERR_INVALID_ARG, "null argument");
+  *block = s->block;
+  *ctas = s->ctas_per_sm;
+  return TP_OK;
+}
+
+void tp_destroy_scene(tp_scene* s) {
+  if (!s) return;
+  if (s->stage_pending) cudaEventSynchronize(s->stage_done);
+  cudaFree(s->d_blob);
+  cudaFree(s->d_sum); cudaFree(s->d_sumsq); cudaFree(s->d_J); cudaFree(s->d_J2);
+  cudaFree(s->d_prefix); cudaFree(s->d_first); cudaFree(s->d_params); cudaFree(s->d_aux);
+  cudaFree(s->d_work); cudaFree(s->d_counters); cudaFree(s->d_status);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->h_aux) cudaFreeHost(s->h_aux);
+  if (s->stage_done) cudaEventDestroy(s->stage_done);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// tp_internal.h -- device data layout shared by the host runtime (tp_api.cu) and
+// the kernels (tp_transport.cu).  Not part of the public ABI (include/tp.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tp.h"
+
+namespace tp {
+
+constexpr int kMaxPar = TP_MAX_PARAMS;
+constexpr int kMaxTallies = TP_MAX_TALLIES;
+constexpr int kNumCounters = 8;
+// Counter slots (also the order of tp_get_counters).
+enum { C_HIST = 0, C_EVENTS, C_COLL, C_CROSS, C_TRUNC, C_LOST, C_MIRROR, C_SEC };
+// History end codes (tp_record.end).
+enum { END_ESCAPED = 0, END_ABSORBED, END_DETECTED, END_BLACK, END_MIRROR, END_TRUNCATED,
+       END_APERTURE, END_LOST };
+// Primitive flag bits.
+enum { F_BIND_RMIN = 1, F_BIND_RMAX = 2 };
+
+// One primitive as the kernels see it.  Lengths in the transport precision R.
+// entry_mask / exit_mask: bit t set if tally t listens to ENTRY / EXIT here.
+template <typename R>
+struct alignas(16) DPrim {
+  R c[3];
+  R p[3];
+  int shape, axis, material, role;
+  int mirror, flags, entry_mask, exit_mask;
+};
+
+// Material: cross sections, bias factors and the location of its Bragg table.
+// Lines are sorted by d descending; cum[cum_off + i] = sum_{j<i} m_j F2_j d_j.
+template <typename R>
+struct alignas(16) DMat {
+  R sig_abs_ref, sig_inc, bragg_pref;  // bragg_pref = 1 / (2 V0^2)
+  R g[TP_NPROC];
+  int abs_1v, nlines, line_off, cum_off;
+  int density_par, scale_par, pad0, pad1;
+};
+
+template <typename R>
+struct alignas(16) DMirror {
+  R m, R0, Qc, alpha, W, mQc, pad0, pad1;
+};
+
+template <typename R>
+struct alignas(16) DTally {
+  R lo[2], hi[2];
+  R inv_w[2];  // nbins / (hi - lo)
+  R origin[3], axis[3];  // axis normalised
+  int kind, trigger, volume, face, scat, nb0, nb1, offset;
+};
+
+// Everything a transport launch needs.  The scene tables live in one blob in
+// global memory (16-byte aligned sections) that each CTA stages into shared
+// memory with a bulk asynchronous copy when it fits.
+template <typename R>
+struct KParams {
+  const uint8_t* blob;
+  uint32_t blob_bytes;
+  uint32_t off_prims, off_mats, off_mirrors, off_tallies, off_line_d, off_line_cum;
+  int stage_blob;  // 1: copy the blob into shared memory
+  int nprim, nmat, ntally, npar;
+  int param_kind[kMaxPar];
+  int radius_par;  // index of the radius parameter or -1
+  R radius_nominal;
+  // world
+  int world_shape;
+  R world_c[3], world_p[3];
+  int world_entry_mask, world_exit_mask;
+  // source
+  int src_kind, src_aperture;
+  R src_c[3], src_half[2], src_lam_lo, src_lam_hi, src_div[2], src_ap[2];
+  // random numbers
+  uint32_t key0, key1;
+  int event_cap;
+  // work: n_inst instances, global history index g in [0, total)
+  int n_inst;
+  const unsigned long long* inst_prefix;  // [n_inst + 1], device
+  const unsigned long long* inst_first;   // [n_inst], device: first history id
+  const double* inst_params;              // [n_inst][kMaxPar], device
+  unsigned long long total;
+  unsigned long long* work_counter;
+  int chunk;  // histories a warp claims at once
+  // outputs
+  double* sum;    // [n_inst][total_bins]
+  double* sumsq;
+  double* J;      // [npar][n_inst][total_bins]
+  double* J2;
+  int total_bins;
+  unsigned long long* counters;  // [kNumCounters]
+  tp_record* records;
+  unsigned long long n_records;
+  int* status;
+};
+
+// Launchers (tp_transport.cu).
+cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block,
+                                 size_t smem, cudaStream_t st);
+cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block,
+                                 size_t smem, cudaStream_t st);
+cudaError_t occupancy_transport(int precision, bool grad, int block, size_t smem, int* ctas);
+cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
+                         double* err, cudaStream_t st);
+cudaError_t launch_backward(const double* J, const double* grad_tallies, const double* scale,
+                            const double* n_done, int n_inst, int npar, int total_bins,
+                            double* grad_params, cudaStream_t st);
+
+}  // namespace tp

@@ -1,0 +1,1000 @@
+// tp_transport.cu -- sm_103a kernels of the biased neutron history loop.
+//
+// One persistent launch processes every history of every instance.  Each warp
+// claims chunks of history ids with one global atomic, and each lane carries
+// one neutron in registers: a lane whose neutron ends takes the next id of its
+// warp's chunk at the top of the next step, so lanes stay busy until the work
+// runs out (no per-history kernel, no host round trip).  A step is one event of
+// the simulation flow of §3.1: cross sections of the current volume, biased
+// flight length (§2.4, Eq. eStepLength2), distance to the next boundary, move
+// and weight compensation (§2.4, Eq. eWeight), then either relocation across
+// the boundary (scorers, supermirror of §2.5) or an interaction (absorption,
+// isotropic incoherent or powder Bragg scattering).
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+// (event k, sub-stream, history id, instance): sub-stream 0 carries flight,
+// process, cosine and azimuth of event k, sub-stream 1 the Bragg line; the source
+// is event 0; a radius-derivative secondary set up at event k uses (k, 2, ..)
+// and secondary s of a history uses sub-streams 4+2s and 5+2s.  Results are thus
+// independent of the launch shape and of which lane ran which history.
+//
+// Tallies are FP64 sums of w and w^2 per bin (plus the score-function tallies),
+// added with warp-aggregated atomics: lanes hitting the same bin combine their
+// values with shuffles and one lane issues the atomic.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "tp_internal.h"
+
+namespace tp {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Precision traits
+// ---------------------------------------------------------------------------
+template <typename R> struct Tr;
+template <> struct Tr<float> {
+  static __device__ __forceinline__ float u01(uint32_t a) {
+    return (float)(a >> 8) * 5.9604644775390625e-8f + 2.98023223876953125e-8f;  // ((a>>8)+1/2) 2^-24
+  }
+  static __device__ __forceinline__ float nudge(float m) { return 1e-5f * fmaxf(1.0f, m); }
+  static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+  static constexpr float kTwoPi = 6.283185307179586f;
+  static constexpr float kFourPi = 12.566370614359172f;
+};
+template <> struct Tr<double> {
+  static __device__ __forceinline__ double u01(uint32_t a) {
+    return ((double)a + 0.5) * 2.3283064365386963e-10;  // (a + 1/2) 2^-32
+  }
+  static __device__ __forceinline__ double nudge(double m) { return 1e-9 * fmax(1.0, m); }
+  static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+  static constexpr double kTwoPi = 6.283185307179586;
+  static constexpr double kFourPi = 12.566370614359172;
+};
+
+__device__ __forceinline__ float d_log(float x) { return logf(x); }
+__device__ __forceinline__ double d_log(double x) { return log(x); }
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ void d_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void d_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float d_tanh(float x) { return tanhf(x); }
+__device__ __forceinline__ double d_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float d_tan(float x) { return tanf(x); }
+__device__ __forceinline__ double d_tan(double x) { return tan(x); }
+__device__ __forceinline__ float d_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double d_atan2(double y, double x) { return atan2(y, x); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Per-lane neutron state
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Particle {
+  R x[3], u[3];
+  R lam, w;
+  R A[kMaxPar];
+  int vol, nscat;
+  uint32_t k, hid, inst, sub0, nsec;
+  int secondary;
+};
+
+template <typename R>
+struct View {
+  const DPrim<R>* prims;
+  const DMat<R>* mats;
+  const DMirror<R>* mirrors;
+  const DTally<R>* tallies;
+  const R* line_d;
+  const R* line_cum;
+};
+
+// ---------------------------------------------------------------------------
+// Cross sections
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int active_lines(const View<R>& V, const DMat<R>& m, R lam) {
+  // lines sorted by d descending: count of 2 d >= lambda by binary search
+  int lo = 0, hi = m.nlines;
+  const R* d = V.line_d + m.line_off;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (R(2) * d[mid] >= lam) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename R>
+__device__ __forceinline__ void sigma(const View<R>& V, int mat, const R* ip, R lam, R sig[TP_NPROC]) {
+  const DMat<R>& m = V.mats[mat];
+  const R dens = m.density_par >= 0 ? ip[m.density_par] : R(1);
+  const R scale = m.scale_par >= 0 ? ip[m.scale_par] : R(1);
+  sig[TP_PROC_ABS] = dens * (m.abs_1v ? m.sig_abs_ref * lam * R(1.0 / 1.8) : m.sig_abs_ref);
+  sig[TP_PROC_INC] = dens * m.sig_inc;
+  R sb = R(0);
+  if (m.nlines > 0) {
+    const int n = active_lines(V, m, lam);
+    sb = dens * scale * m.bragg_pref * lam * lam * V.line_cum[m.cum_off + n];
+  }
+  sig[TP_PROC_BRAGG] = sb;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Radii { R r0, r1, h; };
+
+template <typename R>
+__device__ __forceinline__ Radii<R> radii(const DPrim<R>& p, R dR) {
+  Radii<R> r{p.p[0], p.p[1], p.p[2]};
+  if (p.flags & F_BIND_RMIN) r.r0 += dR;
+  if (p.flags & F_BIND_RMAX) r.r1 += dR;
+  return r;
+}
+
+// local frame: q[0], q[1] transverse, q[2] along the tube axis
+template <typename R>
+__device__ __forceinline__ void to_local(const DPrim<R>& p, const R x[3], const R u[3], R q[3], R v[3]) {
+  const R d0 = x[0] - p.c[0], d1 = x[1] - p.c[1], d2 = x[2] - p.c[2];
+  if (p.shape == TP_TUBE) {
+    if (p.axis == 0) { q[0] = d1; q[1] = d2; q[2] = d0; v[0] = u[1]; v[1] = u[2]; v[2] = u[0]; }
+    else if (p.axis == 1) { q[0] = d2; q[1] = d0; q[2] = d1; v[0] = u[2]; v[1] = u[0]; v[2] = u[1]; }
+    else { q[0] = d0; q[1] = d1; q[2] = d2; v[0] = u[0]; v[1] = u[1]; v[2] = u[2]; }
+  } else {
+    q[0] = d0; q[1] = d1; q[2] = d2; v[0] = u[0]; v[1] = u[1]; v[2] = u[2];
+  }
+}
+
+// Roots of A t^2 + 2 B t + C = 0 with disc = B^2 - A C given; stable form.
+template <typename R>
+__device__ __forceinline__ void roots(R A, R B, R C, R disc, R* t0, R* t1) {
+  const R sq = d_sqrt(disc);
+  const R qq = -(B + copysign(sq, B));
+  R a, b;
+  if (qq != R(0)) { a = qq / A; b = C / qq; } else { a = R(0); b = R(0); }
+  *t0 = fmin(a, b);
+  *t1 = fmax(a, b);
+}
+
+// Quadratic pieces of a tube (2-D, transverse) or sphere (3-D) at radius r.
+template <typename R>
+struct Quad { R A, B, C2, cross2; };
+
+template <typename R>
+__device__ __forceinline__ Quad<R> quad(const R q[3], const R v[3], bool tube) {
+  Quad<R> Q;
+  if (tube) {
+    Q.A = v[0] * v[0] + v[1] * v[1];
+    Q.B = q[0] * v[0] + q[1] * v[1];
+    Q.C2 = q[0] * q[0] + q[1] * q[1];
+    const R c = q[0] * v[1] - q[1] * v[0];
+    Q.cross2 = c * c;
+  } else {
+    Q.A = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    Q.B = q[0] * v[0] + q[1] * v[1] + q[2] * v[2];
+    Q.C2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    const R c0 = q[1] * v[2] - q[2] * v[1], c1 = q[2] * v[0] - q[0] * v[2], c2 = q[0] * v[1] - q[1] * v[0];
+    Q.cross2 = c0 * c0 + c1 * c1 + c2 * c2;
+  }
+  return Q;
+}
+
+// Intersections with radius r: returns false if the ray misses.
+template <typename R>
+__device__ __forceinline__ bool hit_radius(const Quad<R>& Q, R r, R* t0, R* t1) {
+  if (Q.A <= R(0)) return false;
+  const R disc = Q.A * r * r - Q.cross2;  // = B^2 - A (C2 - r^2), no cancellation
+  if (disc < R(0)) return false;
+  roots(Q.A, Q.B, Q.C2 - r * r, disc, t0, t1);
+  return true;
+}
+
+template <typename R>
+__device__ bool inside(const DPrim<R>& p, R dR, const R x[3]) {
+  R q[3], v[3];
+  const R u0[3] = {R(0), R(0), R(1)};
+  to_local(p, x, u0, q, v);
+  if (p.shape == TP_BOX)
+    return fabs(q[0]) <= p.p[0] && fabs(q[1]) <= p.p[1] && fabs(q[2]) <= p.p[2];
+  const Radii<R> rr = radii(p, dR);
+  if (p.shape == TP_TUBE) {
+    const R rho2 = q[0] * q[0] + q[1] * q[1];
+    return rho2 >= rr.r0 * rr.r0 && rho2 <= rr.r1 * rr.r1 && fabs(q[2]) <= rr.h;
+  }
+  const R r2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+  return r2 >= rr.r0 * rr.r0 && r2 <= rr.r1 * rr.r1;
+}
+
+// Distance to leave p from inside; face id out.
+template <typename R>
+__device__ R exit_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int* face) {
+  R q[3], v[3];
+  to_local(p, x, u, q, v);
+  R best = Tr<R>::inf();
+  int bf = -1;
+  if (p.shape == TP_BOX) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (v[a] > R(0)) { const R t = (p.p[a] - q[a]) / v[a]; if (t < best) { best = t; bf = 2 * a + 1; } }
+      else if (v[a] < R(0)) { const R t = (-p.p[a] - q[a]) / v[a]; if (t < best) { best = t; bf = 2 * a; } }
+    }
+  } else {
+    const bool tube = p.shape == TP_TUBE;
+    const Radii<R> rr = radii(p, dR);
+    const Quad<R> Q = quad(q, v, tube);
+    R t0, t1;
+    if (hit_radius(Q, rr.r1, &t0, &t1) && t1 >= R(0) && t1 < best) { best = t1; bf = 0; }
+    if (rr.r0 > R(0) && hit_radius(Q, rr.r0, &t0, &t1) && t0 >= R(0) && t0 < best) { best = t0; bf = 1; }
+    if (tube) {
+      if (v[2] > R(0)) { const R t = (rr.h - q[2]) / v[2]; if (t < best) { best = t; bf = 3; } }
+      else if (v[2] < R(0)) { const R t = (-rr.h - q[2]) / v[2]; if (t < best) { best = t; bf = 2; } }
+    }
+  }
+  *face = bf;
+  return best < R(0) ? R(0) : best;
+}
+
+// Distance to enter p from outside (inf if never); face id out.
+template <typename R>
+__device__ R entry_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int* face) {
+  R q[3], v[3];
+  to_local(p, x, u, q, v);
+  const R INF = Tr<R>::inf();
+  *face = -1;
+  if (p.shape == TP_BOX) {
+    R tn = -INF, tf = INF;
+    int fn = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (v[a] == R(0)) {
+        if (fabs(q[a]) > p.p[a]) return INF;
+        continue;
+      }
+      const R inv = R(1) / v[a];
+      R ta = (-p.p[a] - q[a]) * inv, tb = (p.p[a] - q[a]) * inv;
+      int fa = 2 * a;
+      if (ta > tb) { const R t = ta; ta = tb; tb = t; fa = 2 * a + 1; }
+      if (ta > tn) { tn = ta; fn = fa; }
+      if (tb < tf) tf = tb;
+    }
+    if (tn > tf || tf <= R(0)) return INF;
+    *face = fn;
+    return tn > R(0) ? tn : R(0);
+  }
+  const bool tube = p.shape == TP_TUBE;
+  const Radii<R> rr = radii(p, dR);
+  const Quad<R> Q = quad(q, v, tube);
+  R o0, o1;
+  if (Q.A == R(0)) {
+    if (Q.C2 > rr.r1 * rr.r1) return INF;
+    o0 = -INF; o1 = INF;
+  } else if (!hit_radius(Q, rr.r1, &o0, &o1)) {
+    return INF;
+  }
+  R z0 = -INF, z1 = INF;
+  int fz0 = -1;
+  if (tube) {
+    if (v[2] == R(0)) {
+      if (fabs(q[2]) > rr.h) return INF;
+    } else {
+      const R ta = (-rr.h - q[2]) / v[2], tb = (rr.h - q[2]) / v[2];
+      if (ta < tb) { z0 = ta; z1 = tb; fz0 = 2; } else { z0 = tb; z1 = ta; fz0 = 3; }
+    }
+  }
+  R s0 = o0, e0 = o1, s1 = INF, e1 = -INF;
+  int f0 = 0, f1 = 1;
+  if (rr.r0 > R(0)) {
+    R i0, i1;
+    if (Q.A > R(0) && hit_radius(Q, rr.r0, &i0, &i1)) {
+      e0 = i0; s1 = i1; e1 = o1;
+    } else if (Q.A == R(0) && Q.C2 < rr.r0 * rr.r0) {
+      return INF;
+    }
+  }
+  // first piece
+  R a = s0, b = e0;
+  int f = f0;
+  if (z0 > a) { a = z0; f = fz0; }
+  if (z1 < b) b = z1;
+  if (a < b && b > R(0)) { *face = f; return a > R(0) ? a : R(0); }
+  a = s1; b = e1; f = f1;
+  if (z0 > a) { a = z0; f = fz0; }
+  if (z1 < b) b = z1;
+  if (a < b && b > R(0)) { *face = f; return a > R(0) ? a : R(0); }
+  return INF;
+}
+
+template <typename R>
+__device__ __forceinline__ bool world_inside(const KParams<R>& kp, const R x[3]) {
+  const R d0 = x[0] - kp.world_c[0], d1 = x[1] - kp.world_c[1], d2 = x[2] - kp.world_c[2];
+  if (kp.world_shape == TP_BOX)
+    return fabs(d0) <= kp.world_p[0] && fabs(d1) <= kp.world_p[1] && fabs(d2) <= kp.world_p[2];
+  return d0 * d0 + d1 * d1 + d2 * d2 <= kp.world_p[1] * kp.world_p[1];
+}
+
+template <typename R>
+__device__ __forceinline__ R world_exit(const KParams<R>& kp, const R x[3], const R u[3]) {
+  DPrim<R> w;
+  w.shape = kp.world_shape;
+  w.axis = 2;
+  w.flags = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { w.c[i] = kp.world_c[i]; w.p[i] = kp.world_p[i]; }
+  int f;
+  return exit_dist(w, R(0), x, u, &f);
+}
+
+template <typename R>
+__device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3]) {
+  if (!world_inside(kp, x)) return -2;
+  for (int i = 0; i < kp.nprim; ++i)
+    if (inside(V.prims[i], dR, x)) return i;
+  return -1;
+}
+
+template <typename R>
+__device__ __forceinline__ void normal(const DPrim<R>& p, const R x[3], int face, R n[3]) {
+  n[0] = n[1] = n[2] = R(0);
+  if (p.shape == TP_BOX) { n[face >> 1] = (face & 1) ? R(1) : R(-1); return; }
+  R d[3] = {x[0] - p.c[0], x[1] - p.c[1], x[2] - p.c[2]};
+  if (p.shape == TP_TUBE) {
+    if (face >= 2) { n[p.axis] = (face == 3) ? R(1) : R(-1); return; }
+    d[p.axis] = R(0);
+  }
+  const R inv = (face == 1 ? R(-1) : R(1)) / d_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  n[0] = d[0] * inv; n[1] = d[1] * inv; n[2] = d[2] * inv;
+}
+
+// Deflection by polar cosine mu and azimuth phi about u.
+template <typename R>
+__device__ __forceinline__ void rotate(R u[3], R mu, R phi) {
+  const R st = d_sqrt(fmax(R(0), R(1) - mu * mu));
+  R sp, cp;
+  d_sincos(phi, &sp, &cp);
+  const R t2 = R(1) - u[2] * u[2];
+  R o0, o1, o2;
+  if (t2 > R(1e-20)) {
+    const R t = d_sqrt(t2);
+    const R it = R(1) / t;
+    o0 = mu * u[0] + st * (u[0] * u[2] * cp - u[1] * sp) * it;
+    o1 = mu * u[1] + st * (u[1] * u[2] * cp + u[0] * sp) * it;
+    o2 = mu * u[2] - st * t * cp;
+  } else {
+    o0 = st * cp;
+    o1 = st * sp;
+    o2 = (u[2] >= R(0) ? R(1) : R(-1)) * mu;
+  }
+  u[0] = o0; u[1] = o1; u[2] = o2;
+}
+
+template <typename R>
+__device__ __forceinline__ R mirror_R(const DMirror<R>& m, R Q) {
+  if (Q <= m.Qc) return m.R0;
+  const R r = R(0.5) * m.R0 * (R(1) - m.alpha * (Q - m.Qc)) * (R(1) - d_tanh((Q - m.mQc) / m.W));
+  return r > R(0) ? r : R(0);
+}
+
+// ---------------------------------------------------------------------------
+// Scoring: warp-aggregated FP64 atomics
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void agg_add2(double* a, double* b, unsigned long long idx, double v, double v2) {
+  const unsigned am = __activemask();
+  const unsigned grp = __match_any_sync(am, idx);
+  const int lane = threadIdx.x & 31;
+  if (__any_sync(am, __popc(grp) > 1)) {
+    double s = 0.0, s2 = 0.0;
+    unsigned m = am;
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const double x = __shfl_sync(am, v, src);
+      const double y = __shfl_sync(am, v2, src);
+      if ((grp >> src) & 1u) { s += x; s2 += y; }
+    }
+    v = s;
+    v2 = s2;
+  }
+  if (lane == __ffs(grp) - 1) {
+    atomicAdd(a + idx, v);
+    atomicAdd(b + idx, v2);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ int bin1(R x, R lo, R hi, R inv_w, int n) {
+  if (!(x >= lo) || !(x < hi)) return -1;
+  const int b = (int)floor((x - lo) * inv_w);
+  return (b >= 0 && b < n) ? b : (b >= n ? n - 1 : -1);
+}
+
+template <typename R>
+__device__ __forceinline__ int tally_bin(const DTally<R>& T, const Particle<R>& P) {
+  switch (T.kind) {
+    case TP_TALLY_COUNT: return 0;
+    case TP_TALLY_ANGULAR: {
+      const R v0 = P.x[0] - T.origin[0], v1 = P.x[1] - T.origin[1], v2 = P.x[2] - T.origin[2];
+      const R dt = v0 * T.axis[0] + v1 * T.axis[1] + v2 * T.axis[2];
+      const R c0 = v1 * T.axis[2] - v2 * T.axis[1], c1 = v2 * T.axis[0] - v0 * T.axis[2],
+              c2 = v0 * T.axis[1] - v1 * T.axis[0];
+      const R th = d_atan2(d_sqrt(c0 * c0 + c1 * c1 + c2 * c2), dt);
+      return bin1(th, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    }
+    case TP_TALLY_PSD: {
+      const int bx = bin1(P.x[0], T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      const int by = bin1(P.x[1], T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+      return (bx < 0 || by < 0) ? -1 : bx * T.nb1 + by;
+    }
+    default: {
+      const int bl = bin1(P.lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      const int bx = bin1(P.x[0], T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+      return (bl < 0 || bx < 0) ? -1 : bl * T.nb1 + bx;
+    }
+  }
+}
+
+template <typename R, bool GRAD>
+__device__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>& P, unsigned mask, int face) {
+  while (mask) {
+    const int t = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const DTally<R>& T = V.tallies[t];
+    if (T.face >= 0 && T.face != face) continue;
+    if (T.scat >= 0 && T.scat != P.nscat) continue;
+    const int b = tally_bin(T, P);
+    if (b < 0) continue;
+    const unsigned long long idx = (unsigned long long)P.inst * kp.total_bins + T.offset + b;
+    const double w = (double)P.w;
+    const unsigned long long stride = (unsigned long long)kp.n_inst * kp.total_bins;
+    if (!P.secondary) {
+      agg_add2(kp.sum, kp.sumsq, idx, w, w * w);
+      if (GRAD) {
+        for (int p = 0; p < kp.npar; ++p) {
+          const double g = w * (double)P.A[p];
+          agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
+        }
+      }
+    } else if (GRAD && kp.radius_par >= 0) {
+      agg_add2(kp.J, kp.J2, kp.radius_par * stride + idx, w, w * w);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Source (event 0), §3.2
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R dR, int* end) {
+  const uint4 a = philox(make_uint4(0u, 0u, P.hid, P.inst), kp.key0, kp.key1);
+  P.x[0] = kp.src_c[0]; P.x[1] = kp.src_c[1]; P.x[2] = kp.src_c[2];
+  if (kp.src_kind == TP_SRC_RECT) {
+    P.x[0] += kp.src_half[0] * (R(2) * Tr<R>::u01(a.x) - R(1));
+    P.x[1] += kp.src_half[1] * (R(2) * Tr<R>::u01(a.y) - R(1));
+  }
+  P.lam = kp.src_lam_hi > kp.src_lam_lo ? kp.src_lam_lo + (kp.src_lam_hi - kp.src_lam_lo) * Tr<R>::u01(a.z)
+                                        : kp.src_lam_lo;
+  if (kp.src_div[0] > R(0) || kp.src_div[1] > R(0)) {
+    const uint4 b = philox(make_uint4(0u, 1u, P.hid, P.inst), kp.key0, kp.key1);
+    const R tx = d_tan(kp.src_div[0] * (R(2) * Tr<R>::u01(a.w) - R(1)));
+    const R ty = d_tan(kp.src_div[1] * (R(2) * Tr<R>::u01(b.x) - R(1)));
+    const R inv = R(1) / d_sqrt(tx * tx + ty * ty + R(1));
+    P.u[0] = tx * inv; P.u[1] = ty * inv; P.u[2] = inv;
+  } else {
+    P.u[0] = R(0); P.u[1] = R(0); P.u[2] = R(1);
+  }
+  P.w = R(1);
+#pragma unroll
+  for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
+  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0;
+  if (kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
+                          fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
+    P.w = R(0);
+    *end = END_APERTURE;
+    return false;
+  }
+  P.vol = locate(kp, V, dR, P.x);
+  if (P.vol == -2) { *end = END_LOST; return false; }
+  if (P.vol >= 0 && V.prims[P.vol].role != TP_ROLE_BULK) { *end = END_BLACK; return false; }
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ R nudge_len(const R x[3]) {
+  return Tr<R>::nudge(fmax(fabs(x[0]), fmax(fabs(x[1]), fabs(x[2]))));
+}
+
+// Draw the new direction of a scatter by process `proc` of material `mat`.
+template <typename R>
+__device__ __forceinline__ void scatter_dir(const View<R>& V, int mat, int proc, R lam, R u[3], R xmu,
+                                            R xphi, R xline) {
+  if (proc == TP_PROC_INC) {
+    const R mu = R(2) * xmu - R(1);
+    const R st = d_sqrt(fmax(R(0), R(1) - mu * mu));
+    R sp, cp;
+    d_sincos(Tr<R>::kTwoPi * xphi, &sp, &cp);
+    u[0] = st * cp; u[1] = st * sp; u[2] = mu;
+  } else {
+    const DMat<R>& m = V.mats[mat];
+    const int n = active_lines(V, m, lam);
+    const R* cum = V.line_cum + m.cum_off;
+    const R target = xline * cum[n];
+    // smallest i < n with target < cum[i+1]
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (target < cum[mid + 1]) hi = mid; else lo = mid + 1;
+    }
+    const R sb = lam / (R(2) * V.line_d[m.line_off + lo]);
+    rotate(u, R(1) - R(2) * sb * sb, Tr<R>::kTwoPi * xphi);
+  }
+}
+
+// Radius derivative at the crossing of a lateral surface that moves with the
+// radius parameter.  The layer of thickness dR just outside the surface turns
+// from the outer material into the inner one; a path crossing it with |n.u|
+// spends dR/|n.u| in it.  The continuing path's score function gains
+// -(Sigma_t,in - Sigma_t,out)/|n.u|; the collisions that now happen in the layer
+// are added as one derivative secondary starting at the crossing, with weight
+// w sign(c) C/|n.u|, scattered by a term picked with probability |c|/C among
+// c = +Sigma_j,in, -Sigma_j,out over the scattering processes j.  Returns true
+// if a secondary was created in *S.
+template <typename R>
+__device__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
+                                R dR, int mi, int mo, const R n[3], Particle<R>* S,
+                                unsigned long long* cnt) {
+  const R cosn = fabs(P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2]);
+  if (cosn < R(1e-12)) return false;
+  R si[TP_NPROC] = {R(0), R(0), R(0)}, so[TP_NPROC] = {R(0), R(0), R(0)};
+  if (mi >= 0) sigma(V, mi, ip, P.lam, si);
+  if (mo >= 0) sigma(V, mo, ip, P.lam, so);
+  P.A[kp.radius_par] -= ((si[0] + si[1] + si[2]) - (so[0] + so[1] + so[2])) / cosn;
+  const R term[4] = {si[TP_PROC_INC], si[TP_PROC_BRAGG], -so[TP_PROC_INC], -so[TP_PROC_BRAGG]};
+  const R C = fabs(term[0]) + fabs(term[1]) + fabs(term[2]) + fabs(term[3]);
+  if (!(C > R(0))) return false;
+  const uint4 r = philox(make_uint4(P.k, 2u, P.hid, P.inst), kp.key0, kp.key1);
+  const R pickv = Tr<R>::u01(r.x) * C;
+  int pick = 3;
+  R acc = R(0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    acc += fabs(term[i]);
+    if (pick == 3 && i < 3 && pickv < acc) pick = i;
+  }
+  while (term[pick] == R(0) && pick > 0) --pick;
+  const int mat = pick < 2 ? mi : mo;
+  const int proc = (pick & 1) ? TP_PROC_BRAGG : TP_PROC_INC;
+  *S = P;
+  S->secondary = 1;
+  S->w = P.w * (term[pick] > R(0) ? R(1) : R(-1)) * C / cosn;
+  S->nscat = P.nscat + 1;
+  S->sub0 = 4u + 2u * P.nsec;
+  S->k = 0;
+  P.nsec++;
+  scatter_dir(V, mat, proc, P.lam, S->u, Tr<R>::u01(r.y), Tr<R>::u01(r.z), Tr<R>::u01(r.w));
+  cnt[C_SEC]++;
+  const R e = nudge_len(S->x);
+  R xn[3] = {S->x[0] + e * S->u[0], S->x[1] + e * S->u[1], S->x[2] + e * S->u[2]};
+  const int v = locate(kp, V, dR, xn);
+  if (v < -1) return false;
+  S->x[0] = xn[0]; S->x[1] = xn[1]; S->x[2] = xn[2];
+  S->vol = v;
+  if (v >= 0 && V.prims[v].role != TP_ROLE_BULK) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// One event of one neutron.  Returns -1 while alive, else the end code.
+// spawn: set when a radius-derivative secondary was created into *S.
+// ---------------------------------------------------------------------------
+template <typename R, bool GRAD>
+__device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+                    unsigned long long* cnt, Particle<R>* S, bool* spawn) {
+  const R INF = Tr<R>::inf();
+  P.k += 1;
+  if ((int)P.k > kp.event_cap) { cnt[C_TRUNC]++; return END_TRUNCATED; }
+  cnt[C_EVENTS]++;
+  const uint4 r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
+  const int mat = P.vol >= 0 ? V.prims[P.vol].material : -1;
+  R sig[TP_NPROC] = {R(0), R(0), R(0)};
+  R sig_t = R(0), sig_g = R(0);
+  if (mat >= 0) {
+    sigma(V, mat, ip, P.lam, sig);
+    const DMat<R>& m = V.mats[mat];
+    sig_t = sig[0] + sig[1] + sig[2];
+    sig_g = m.g[0] * sig[0] + m.g[1] * sig[1] + m.g[2] * sig[2];
+  }
+  const R l = sig_g > R(0) ? -d_log(Tr<R>::u01(r0.x)) / sig_g : INF;
+  // next boundary
+  R db;
+  int target = -3, face = -1;
+  if (P.vol >= 0) {
+    db = exit_dist(V.prims[P.vol], dR, P.x, P.u, &face);
+  } else {
+    db = world_exit(kp, P.x, P.u);
+    for (int i = 0; i < kp.nprim; ++i) {
+      int f;
+      const R t = entry_dist(V.prims[i], dR, P.x, P.u, &f);
+      if (t < db) { db = t; target = i; face = f; }
+    }
+  }
+  const bool cross = l >= db;
+  const R x = cross ? db : l;
+  if (!(x < INF)) { cnt[C_LOST]++; return END_LOST; }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) P.x[i] += x * P.u[i];
+  if (sig_g != sig_t) P.w *= d_exp((sig_g - sig_t) * x);
+  if (GRAD && mat >= 0 && !P.secondary) {
+    const DMat<R>& m = V.mats[mat];
+    for (int p = 0; p < kp.npar; ++p) {
+      if (kp.param_kind[p] == TP_PAR_DENSITY && m.density_par == p) P.A[p] -= sig_t * x;
+      if (kp.param_kind[p] == TP_PAR_SCALE && m.scale_par == p) P.A[p] -= sig[TP_PROC_BRAGG] * x;
+    }
+  }
+  if (cross) {
+    cnt[C_CROSS]++;
+    if (P.vol >= 0) {
+      // leave the current primitive: EXIT scorers, then relocate
+      const int from = P.vol;
+      const DPrim<R>& pf = V.prims[from];
+      if (pf.exit_mask) score<R, GRAD>(kp, V, P, (unsigned)pf.exit_mask, face);
+      const R e = nudge_len(P.x);
+      R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
+      const int v = locate(kp, V, dR, xn);
+      if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
+          ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
+        R n[3];
+        normal(pf, P.x, face, n);
+        const int mnext = v >= 0 ? V.prims[v].material : -1;
+        const int mi = face == 0 ? pf.material : mnext;
+        const int mo = face == 0 ? mnext : pf.material;
+        *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
+      }
+      P.x[0] = xn[0]; P.x[1] = xn[1]; P.x[2] = xn[2];
+      if (v == -2) {
+        if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
+        return END_ESCAPED;
+      }
+      P.vol = v;
+      if (v >= 0) {
+        const DPrim<R>& pt = V.prims[v];
+        if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, -1);
+        if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
+        if (pt.role == TP_ROLE_BLACK) return END_BLACK;
+      }
+      return -1;
+    }
+    if (target == -3) {
+      if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
+      return END_ESCAPED;
+    }
+    const DPrim<R>& pt = V.prims[target];
+    if (pt.mirror >= 0) {
+      // supermirror: weight R(Q), specular reflection (Eq. eMirrowNewDir)
+      R n[3];
+      normal(pt, P.x, face, n);
+      const R un = P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2];
+      const R Q = Tr<R>::kFourPi * fabs(un) / P.lam;
+      const R Rf = mirror_R(V.mirrors[pt.mirror], Q);
+      cnt[C_MIRROR]++;
+      P.w *= Rf;
+      if (!(Rf > R(0))) return END_MIRROR;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) P.u[i] -= R(2) * n[i] * un;
+      const R e = nudge_len(P.x);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
+      return -1;
+    }
+    if (GRAD && kp.radius_par >= 0 && !P.secondary && pt.shape != TP_BOX &&
+        ((face == 0 && (pt.flags & F_BIND_RMAX)) || (face == 1 && (pt.flags & F_BIND_RMIN)))) {
+      R n[3];
+      normal(pt, P.x, face, n);
+      const int mi = face == 0 ? pt.material : -1;
+      const int mo = face == 0 ? -1 : pt.material;
+      *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
+    }
+    const R e = nudge_len(P.x);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
+    P.vol = target;
+    if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
+    if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
+    if (pt.role == TP_ROLE_BLACK) return END_BLACK;
+    return -1;
+  }
+  // ---- interaction ----
+  cnt[C_COLL]++;
+  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid < kp.n_records) {
+    tp_record* rc = kp.records + P.hid;
+    rc->first_collision[0] = (double)P.x[0];
+    rc->first_collision[1] = (double)P.x[1];
+    rc->first_collision[2] = (double)P.x[2];
+  }
+  const DMat<R>& m = V.mats[mat];
+  const R xi1 = Tr<R>::u01(r0.y) * sig_g;
+  int j;
+  const R c0 = m.g[0] * sig[0], c1 = c0 + m.g[1] * sig[1];
+  if (xi1 < c0) j = 0;
+  else if (xi1 < c1) j = 1;
+  else if (m.g[2] * sig[2] > R(0)) j = 2;
+  else j = (m.g[1] * sig[1] > R(0)) ? 1 : 0;
+  P.w /= m.g[j];
+  if (GRAD && !P.secondary) {
+    for (int p = 0; p < kp.npar; ++p) {
+      if (kp.param_kind[p] == TP_PAR_DENSITY && m.density_par == p) P.A[p] += R(1);
+      if (kp.param_kind[p] == TP_PAR_SCALE && m.scale_par == p && j == TP_PROC_BRAGG) P.A[p] += R(1);
+    }
+  }
+  if (j == TP_PROC_ABS) return END_ABSORBED;
+  R xline = R(0);
+  if (j == TP_PROC_BRAGG) {
+    const uint4 r1 = philox(make_uint4(P.k, P.sub0 + 1u, P.hid, P.inst), kp.key0, kp.key1);
+    xline = Tr<R>::u01(r1.x);
+  }
+  scatter_dir(V, mat, j, P.lam, P.u, Tr<R>::u01(r0.z), Tr<R>::u01(r0.w), xline);
+  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid < kp.n_records) {
+    tp_record* rc = kp.records + P.hid;
+    rc->dir_after_first[0] = (double)P.u[0];
+    rc->dir_after_first[1] = (double)P.u[1];
+    rc->dir_after_first[2] = (double)P.u[2];
+  }
+  P.nscat++;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copy of the scene tables into shared memory
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Returns false if the wait gave up (status set by the caller).
+__device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+  }
+  // bounded wait on phase 0
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 20) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar))
+        : "memory");
+  }
+  return __syncthreads_and(done) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// The persistent transport kernel
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& P, int end) {
+  if (kp.records && !P.secondary && P.inst == 0 && P.hid < kp.n_records) {
+    tp_record* rc = kp.records + P.hid;
+    rc->final_pos[0] = (double)P.x[0];
+    rc->final_pos[1] = (double)P.x[1];
+    rc->final_pos[2] = (double)P.x[2];
+    rc->w_final = (double)P.w;
+    for (int i = 0; i < kMaxPar; ++i) rc->A_final[i] = (double)P.A[i];
+    rc->nscat = P.nscat;
+    rc->nevents = (int)P.k;
+    rc->end = end;
+  }
+}
+
+template <typename R, bool GRAD>
+__global__ void __launch_bounds__(512) k_transport(const __grid_constant__ KParams<R> kp) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bar;
+  const uint8_t* base = kp.blob;
+  if (kp.stage_blob) {
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
+      if (threadIdx.x == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+      return;
+    }
+    base = smem;
+  }
+  View<R> V;
+  V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
+  V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
+  V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
+  V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
+  V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
+
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned long long cnt[kNumCounters];
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+
+  Particle<R> P, park, S;
+  R ip[kMaxPar];
+  R dR = R(0);
+  bool alive = false, done = false, parked = false;
+  unsigned long long chunk_next = 0, chunk_end = 0;  // warp-uniform
+
+  for (;;) {
+    // ---- give idle lanes new histories from the warp's chunk ----
+    unsigned idle = __ballot_sync(kFull, !alive && !done);
+    while (idle) {
+      if (chunk_next >= chunk_end) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+        b = __shfl_sync(kFull, b, 0);
+        if (b >= kp.total) {
+          if (!alive) done = true;
+          break;
+        }
+        chunk_next = b;
+        chunk_end = min(b + (unsigned long long)kp.chunk, kp.total);
+      }
+      const unsigned avail = (unsigned)min((unsigned long long)__popc(idle), chunk_end - chunk_next);
+      const unsigned rank = __popc(idle & lt_mask);
+      if (((idle >> lane) & 1u) && rank < avail) {
+        const unsigned long long g = chunk_next + rank;
+        // instance of global index g
+        int lo = 0, hi = kp.n_inst - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        P.inst = (uint32_t)lo;
+        P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
+#pragma unroll
+        for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)kp.inst_params[(size_t)lo * kMaxPar + i];
+        dR = kp.radius_par >= 0 ? ip[kp.radius_par] - kp.radius_nominal : R(0);
+        cnt[C_HIST]++;
+        int end = -1;
+        alive = source(kp, V, P, dR, &end);
+        if (!alive) {
+          if (end == END_LOST) cnt[C_LOST]++;
+          finish(kp, P, end);
+        }
+      }
+      chunk_next += avail;
+      idle = __ballot_sync(kFull, !alive && !done);
+    }
+    if (__all_sync(kFull, done)) break;
+    if (alive) {
+      bool spawn = false;
+      const int end = step<R, GRAD>(kp, V, P, ip, dR, cnt, &S, &spawn);
+      if (end >= 0) finish(kp, P, end);
+      if (GRAD && spawn) {
+        if (end < 0) { park = P; parked = true; }
+        P = S;
+      } else if (end >= 0) {
+        if (GRAD && parked) { P = park; parked = false; }
+        else alive = false;
+      }
+    }
+  }
+  // ---- counters: warp sum, one atomic per warp and slot ----
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) {
+    unsigned long long v = cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0 && v) atomicAdd(kp.counters + i, v);
+  }
+}
+
+// mean and standard error per bin
+__global__ void k_stats(const double* __restrict__ sum, const double* __restrict__ sumsq, double n,
+                        int nbins, double* __restrict__ mean, double* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbins) return;
+  const double m = n > 0 ? sum[i] / n : 0.0;
+  mean[i] = m;
+  if (err) {
+    const double var = n > 0 ? fmax(sumsq[i] / n - m * m, 0.0) : 0.0;
+    err[i] = n > 1 ? sqrt(var / (n - 1.0)) : 0.0;
+  }
+}
+
+// grad_params[i][p] = scale[i][p] / N_i * sum_b grad[i][b] J[p][i][b]; one CTA per (i, p)
+__global__ void k_backward(const double* __restrict__ J, const double* __restrict__ grad,
+                           const double* __restrict__ scale, const double* __restrict__ n_done,
+                           int n_inst, int npar, int total_bins, double* __restrict__ out) {
+  const int i = blockIdx.x, p = blockIdx.y;
+  const double* Jp = J + ((size_t)p * n_inst + i) * total_bins;
+  const double* g = grad + (size_t)i * total_bins;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < total_bins; b += blockDim.x) acc += g[b] * Jp[b];
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (threadIdx.x == 0) {
+      const double n = n_done[i];
+      out[(size_t)i * npar + p] = n > 0 ? acc * scale[(size_t)i * npar + p] / n : 0.0;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  if (grad) k_transport<float, true><<<grid, block, smem, st>>>(p);
+  else k_transport<float, false><<<grid, block, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  if (grad) k_transport<double, true><<<grid, block, smem, st>>>(p);
+  else k_transport<double, false><<<grid, block, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+static cudaError_t set_smem(const void* fn, size_t smem) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t occupancy_transport(int precision, bool grad, int block, size_t smem, int* ctas) {
+  const void* fn;
+  if (precision == TP_FP64) fn = grad ? (const void*)k_transport<double, true> : (const void*)k_transport<double, false>;
+  else fn = grad ? (const void*)k_transport<float, true> : (const void*)k_transport<float, false>;
+  cudaError_t e = set_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+}
+
+cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
+                         double* err, cudaStream_t st) {
+  if (nbins <= 0) return cudaSuccess;
+  k_stats<<<(nbins + 255) / 256, 256, 0, st>>>(sum, sumsq, n, nbins, mean, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const double* J, const double* grad_tallies, const double* scale,
+                            const double* n_done, int n_inst, int npar, int total_bins,
+                            double* grad_params, cudaStream_t st) {
+  if (n_inst <= 0 || npar <= 0) return cudaSuccess;
+  k_backward<<<dim3(n_inst, npar), 256, 0, st>>>(J, grad_tallies, scale, n_done, n_inst, npar, total_bins,
+                                                 grad_params);
+  return cudaGetLastError();
+}
+
+}  // namespace tp

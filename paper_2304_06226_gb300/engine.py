@@ -1,0 +1,240 @@
+"""High-level use of the C ABI from Python with PyTorch device memory and streams.
+
+`Scene` marshals a workload description (module `workloads`) into the tp_*
+structures and owns the library handle; `TransportFn` is the
+torch.autograd.Function whose forward runs the histories and whose backward
+calls tp_backward.  Nothing here computes transport: it moves arguments."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import native as N
+
+_SHAPES = {"box": N.TP_BOX, "tube": N.TP_TUBE, "sphere": N.TP_SPHERE}
+_ROLES = {"bulk": N.TP_ROLE_BULK, "detector": N.TP_ROLE_DETECTOR, "black": N.TP_ROLE_BLACK}
+_TALLY = {"count": N.TP_TALLY_COUNT, "angular": N.TP_TALLY_ANGULAR, "psd": N.TP_TALLY_PSD,
+          "wlx": N.TP_TALLY_WLX}
+_PTS = {"entry": N.TP_PTS_ENTRY, "exit": N.TP_PTS_EXIT}
+_PAR = {"radius": N.TP_PAR_RADIUS, "scale": N.TP_PAR_SCALE, "density": N.TP_PAR_DENSITY}
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Scene:
+    """A scene on the current CUDA device built from a workload description."""
+
+    def __init__(self, desc: dict, precision: str | None = None):
+        self.desc = desc
+        self._keep = []
+        prec = precision or desc.get("precision", "f32")
+        prims = desc["prims"]
+        mirrors = []
+        P = (N.tp_prim * max(1, len(prims)))()
+        for i, p in enumerate(prims):
+            mi = -1
+            if p.get("mirror"):
+                mi = len(mirrors)
+                mirrors.append(p["mirror"])
+            P[i] = N.tp_prim(_SHAPES[p["shape"]], p["axis"], p["material"], _ROLES[p["role"]], mi,
+                             int(p["bind_rmin"]), int(p["bind_rmax"]), N.D3(*p["centre"]),
+                             N.D3(*p["params"]))
+        M = (N.tp_mirror * max(1, len(mirrors)))()
+        for i, m in enumerate(mirrors):
+            M[i] = N.tp_mirror(m["m"], m["R0"], m["Qc"], m["alpha"], m["W"])
+        src = desc["source"]
+        ap = src.get("aperture")
+        S = N.tp_source(N.TP_SRC_RECT if src["kind"] == "rect" else N.TP_SRC_PENCIL,
+                        N.D3(*src["centre"]), N.D2(*src["half"]), src["lambda"][0], src["lambda"][1],
+                        N.D2(*src["div"]), 1 if ap else 0, N.D2(*(ap if ap else (0.0, 0.0))))
+        tallies = desc["tallies"]
+        T = (N.tp_tally_desc * max(1, len(tallies)))()
+        for i, t in enumerate(tallies):
+            T[i] = N.tp_tally_desc(_TALLY[t["kind"]], _PTS[t["trigger"]], t["volume"], t["face"],
+                                   t["scat"], N.I2(*t["bins"]), N.D2(*t["lo"]), N.D2(*t["hi"]),
+                                   N.D3(*t["origin"]), N.D3(*t["axis"]))
+        inst = desc["instances"]
+        params = np.ascontiguousarray(inst["params"], dtype=np.float64)
+        self.n_inst = int(params.shape[0])
+        self.n_par = len(desc["params"])
+        pk = np.array([_PAR[p["kind"]] for p in desc["params"]] or [0], dtype=np.int32)
+        pflat = np.ascontiguousarray(params.reshape(-1)) if self.n_par else np.zeros(1)
+        self._keep += [P, M, T, pk, pflat]
+        w = desc["world"]
+        d = N.tp_scene_desc(_SHAPES[w["shape"]], N.D3(*w["centre"]), N.D3(*w["params"]),
+                            len(prims), P, len(mirrors), M, S, len(tallies), T, self.n_inst,
+                            pflat.ctypes.data_as(N.DP), self.n_par,
+                            pk.ctypes.data_as(C.POINTER(C.c_int)),
+                            float(inst.get("radius_nominal", 0.0)),
+                            N.TP_FP64 if prec == "f64" else N.TP_FP32, int(desc.get("event_cap", 0)))
+        self.handle = N.tp_create_scene(d)
+        self.precision = prec
+        self.params = params.copy()
+        self.tally_bins = [t["bins"][0] * t["bins"][1] for t in tallies]
+        self.tally_off = np.concatenate([[0], np.cumsum(self.tally_bins)]).astype(int).tolist()
+        self.total_bins = N.tp_total_bins(self.handle)
+        self.counts = np.asarray(inst["counts"], dtype=np.int64)
+        self.seed = int(desc.get("seed", 4096))
+        self.set_materials(desc["materials"])
+        bias = np.asarray(desc["bias"], dtype=np.float64).reshape(-1, 3)
+        for m in range(bias.shape[0]):
+            N.tp_set_bias(self.handle, m, bias[m])
+
+    # ------------------------------------------------------------------
+    def set_materials(self, mats) -> None:
+        arr = []
+        for m in mats:
+            br = m.get("bragg")
+            if br:
+                d = np.ascontiguousarray(br["d"], dtype=np.float64)
+                mu = np.ascontiguousarray(br["mult"], dtype=np.float64)
+                f2 = np.ascontiguousarray(br["F2"], dtype=np.float64)
+                self._keep += [d, mu, f2]
+                arr.append(N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"),
+                                         m["sigma_inc"], len(d), br["V0"], d.ctypes.data_as(N.DP),
+                                         mu.ctypes.data_as(N.DP), f2.ctypes.data_as(N.DP),
+                                         m["density_param"], m["scale_param"]))
+            else:
+                arr.append(N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"),
+                                         m["sigma_inc"], 0, 1.0, None, None, None,
+                                         m["density_param"], m["scale_param"]))
+        N.tp_set_materials(self.handle, arr)
+
+    def set_bias(self, material: int, g) -> None:
+        N.tp_set_bias(self.handle, material, g)
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(self.n_inst, self.n_par)
+        N.tp_set_params(self.handle, p)
+        self.params = p.copy()
+
+    def reset(self) -> None:
+        N.tp_reset_tallies(self.handle)
+
+    def run(self, n=None, seed: int | None = None, first=None, want_grad: bool = False, stream=None,
+            block_size: int = 0, ctas_per_sm: int = 0, records: torch.Tensor | None = None) -> None:
+        """Queue histories on `stream` (default: torch's current stream).  n: per
+        instance counts (int for one instance, array for many; default: the
+        workload's counts)."""
+        counts = self.counts if n is None else np.broadcast_to(np.asarray(n, dtype=np.uint64),
+                                                               (self.n_inst,))
+        cnt = np.ascontiguousarray(counts, dtype=np.uint64)
+        fst = None if first is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(first, dtype=np.uint64), (self.n_inst,)))
+        self._run_keep = (cnt, fst)
+        r = N.tp_run(seed if seed is not None else self.seed,
+                     cnt.ctypes.data_as(C.POINTER(C.c_uint64)),
+                     None if fst is None else fst.ctypes.data_as(C.POINTER(C.c_uint64)),
+                     int(want_grad), _stream_handle(stream), block_size, ctas_per_sm,
+                     None if records is None else records.data_ptr(),
+                     0 if records is None else records.numel() // C.sizeof(N.tp_record))
+        N.tp_run_histories(self.handle, r)
+
+    def tally(self, t: int, instance: int = 0, device: bool = True):
+        nb = self.tally_bins[t]
+        if device:
+            mean = torch.empty(nb, dtype=torch.float64, device="cuda")
+            err = torch.empty(nb, dtype=torch.float64, device="cuda")
+            N.tp_read_tallies(self.handle, t, instance, mean.data_ptr(), err.data_ptr(), True)
+            torch.cuda.synchronize()
+            return mean, err
+        mean = np.empty(nb)
+        err = np.empty(nb)
+        N.tp_read_tallies(self.handle, t, instance, mean.ctypes.data, err.ctypes.data, False)
+        return mean, err
+
+    def raw(self, instance: int = 0) -> dict:
+        tb = self.total_bins
+        out = {k: np.zeros(tb) for k in ("sum", "sumsq")}
+        npar = max(1, self.n_par)
+        out["J"] = np.zeros((npar, tb))
+        out["J2"] = np.zeros((npar, tb))
+        N.tp_read_raw(self.handle, instance, out["sum"].ctypes.data, out["sumsq"].ctypes.data,
+                      out["J"].ctypes.data if self.n_par else None,
+                      out["J2"].ctypes.data if self.n_par else None, False)
+        out["J"] = out["J"][: self.n_par]
+        out["J2"] = out["J2"][: self.n_par]
+        return out
+
+    def counters(self) -> dict:
+        return N.tp_get_counters(self.handle)
+
+    def launch(self) -> tuple[int, int]:
+        return N.tp_get_launch(self.handle)
+
+    def means(self) -> torch.Tensor:
+        """Per-instance means of every bin, [n_inst, total_bins] float64 on the GPU."""
+        out = torch.empty(self.n_inst, self.total_bins, dtype=torch.float64, device="cuda")
+        for q in range(self.n_inst):
+            for t in range(len(self.tally_bins)):
+                o = self.tally_off[t]
+                N.tp_read_tallies(self.handle, t, q, out[q, o:].data_ptr(), None, True)
+        return out
+
+    def backward(self, grad: torch.Tensor, stream=None) -> torch.Tensor:
+        g = grad.to(device="cuda", dtype=torch.float64).contiguous()
+        out = torch.empty(self.n_inst, self.n_par, dtype=torch.float64, device="cuda")
+        N.tp_backward(self.handle, g.data_ptr(), out.data_ptr(), True, _stream_handle(stream))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            N.tp_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def new_records(n: int) -> torch.Tensor:
+    """Device buffer for n tp_record, first-collision fields set to NaN."""
+    rs = C.sizeof(N.tp_record)
+    assert rs % 8 == 0
+    buf = torch.zeros(n * rs // 8, dtype=torch.float64, device="cuda")
+    v = buf.view(n, rs // 8)
+    v[:, 0:6] = math.nan
+    return buf
+
+
+def records_to_numpy(buf: torch.Tensor) -> dict:
+    rs = C.sizeof(N.tp_record)
+    raw = buf.cpu().numpy().view(np.uint8)
+    n = raw.size // rs
+    dt = np.dtype([("first_collision", "f8", 3), ("dir_after_first", "f8", 3), ("final_pos", "f8", 3),
+                   ("w_final", "f8"), ("A_final", "f8", N.TP_MAX_PARAMS), ("nscat", "i4"),
+                   ("nevents", "i4"), ("end", "i4"), ("pad", "i4")])
+    assert dt.itemsize == rs
+    arr = raw[: n * rs].view(dt)
+    return {k: arr[k].copy() for k in dt.names if k != "pad"}
+
+
+class TransportFn(torch.autograd.Function):
+    """Tally means as a differentiable function of the instance parameters.
+
+    forward(params [n_inst, n_par]) sets the parameters, runs the histories with
+    the score-function accumulators on, and returns the per-instance means of
+    every bin [n_inst, total_bins]; backward contracts the incoming gradient
+    with the accumulated derivative tallies (tp_backward)."""
+
+    @staticmethod
+    def forward(ctx, params: torch.Tensor, scene: Scene, n=None, seed: int | None = None):
+        scene.set_params(params.detach().cpu().numpy())
+        scene.reset()
+        scene.run(n=n, seed=seed, want_grad=True)
+        ctx.scene = scene
+        return scene.means()
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        g = ctx.scene.backward(grad_out)
+        return g.to(grad_out.device), None, None, None

@@ -1,0 +1,269 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+FP64 runs share Philox streams with the oracle history by history, so they are
+compared history by history (first-collision positions to 1e-9 relative) and
+tally by tally.  FP32 runs are compared statistically: at least 99 % of the
+non-empty bins within 3 combined standard errors, none beyond 5, chi-square
+p >= 1e-3, and integrated totals within 1e-3 relative or 4 standard errors."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from stats import compare_tallies, stats
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as G
+    G.build()
+    from paper_2304_06226_gb300 import engine
+    return engine
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def gpu_run(eng, desc, n, records=0, want_grad=False, seed=None, **kw):
+    sc = eng.Scene(desc)
+    rec = eng.new_records(records) if records else None
+    sc.run(n, records=rec, want_grad=want_grad, seed=seed, **kw)
+    torch.cuda.synchronize()
+    out = {"scene": sc, "raw": sc.raw(0), "counters": sc.counters()}
+    if rec is not None:
+        out["records"] = eng.records_to_numpy(rec)
+    return out
+
+
+def assert_totals(m1, e1, m2, e2, rel=1e-3, nsig=4.0):
+    t1, t2 = m1.sum(), m2.sum()
+    s = math.sqrt((e1 ** 2).sum() + (e2 ** 2).sum())
+    assert abs(t1 - t2) <= max(rel * abs(t2), nsig * s), (t1, t2, s)
+
+
+# ---------------------------------------------------------------------------
+# Workload 1 (slab, FP64): history by history
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("g", [1.0, 3.0])
+def test_slab_fp64_histories_match_oracle(eng, orc, g):
+    n = 50_000
+    desc = W.slab(g=g, n_histories=n, precision="f64")
+    gpu = gpu_run(eng, desc, n, records=n)
+    o = orc.OracleScene(desc).run(n, records=True)
+    gr, orr = gpu["records"], o["records"]
+    same_nan = np.isnan(gr["first_collision"][:, 0]) == np.isnan(orr["first_collision"][:, 0])
+    assert same_nan.mean() >= 0.9999
+    both = ~np.isnan(gr["first_collision"][:, 0]) & ~np.isnan(orr["first_collision"][:, 0])
+    rel = np.abs(gr["first_collision"][both] - orr["first_collision"][both]) / np.maximum(
+        1.0, np.abs(orr["first_collision"][both]))
+    assert rel.max() <= 1e-9
+    same = (gr["end"] == orr["end"]) & (gr["nscat"] == orr["nscat"]) & (gr["nevents"] == orr["nevents"])
+    assert same.mean() >= 0.9999
+    wrel = np.abs(gr["w_final"][same] - orr["w_final"][same]) / np.maximum(1e-300, np.abs(orr["w_final"][same]))
+    assert np.nanmax(wrel) <= 1e-9
+    # tallies: identical histories, different summation order
+    assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(gpu["raw"]["sumsq"], o["sumsq"], rtol=1e-9, atol=1e-12)
+    c = gpu["counters"]
+    for k in ("histories", "events", "collisions", "crossings", "truncated", "lost"):
+        assert abs(c[k] - o["counters"][k]) <= max(2, 1e-4 * o["counters"][k]), k
+
+
+def test_slab_fp32_statistics_and_uncollided_closed_form(eng, orc):
+    n = 1_000_000
+    desc = W.slab(g=3.0, n_histories=n, precision="f32")
+    gpu = gpu_run(eng, desc, n)
+    o = orc.OracleScene(desc).run(n)
+    m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
+    m2, e2 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    assert abs(m1[0] - math.exp(-0.6)) < 4 * e1[0]
+
+
+def test_slab_first_history_offset_and_split_runs_add_up(eng):
+    """Runs over [0, a) and [a, n) equal one run over [0, n) (FP64)."""
+    n, a = 40_000, 17_003
+    desc = W.slab(g=3.0, n_histories=n, precision="f64")
+    whole = gpu_run(eng, desc, n)["raw"]
+    sc = eng.Scene(desc)
+    sc.run(a)
+    sc.run(n - a, first=a)
+    torch.cuda.synchronize()
+    parts = sc.raw(0)
+    assert np.allclose(parts["sum"], whole["sum"], rtol=1e-12, atol=1e-12)
+    assert np.allclose(parts["sumsq"], whole["sumsq"], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("block,ctas", [(32, 1), (128, 0), (512, 0), (256, 1)])
+def test_launch_shape_does_not_change_results(eng, block, ctas):
+    n = 30_011   # ragged against every chunk size
+    desc = W.slab(g=3.0, n_histories=n, precision="f64")
+    ref = gpu_run(eng, desc, n)["raw"]
+    got = gpu_run(eng, desc, n, block_size=block, ctas_per_sm=ctas)["raw"]
+    assert np.allclose(got["sum"], ref["sum"], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 33])
+def test_tiny_and_empty_runs(eng, orc, n):
+    desc = W.slab(g=1.0, n_histories=max(n, 1), precision="f64")
+    gpu = gpu_run(eng, desc, n)
+    assert gpu["counters"]["histories"] == n
+    if n:
+        o = orc.OracleScene(desc).run(n)
+        assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+    else:
+        assert not gpu["raw"]["sum"].any()
+
+
+# ---------------------------------------------------------------------------
+# Workload 2 (powder, FP32)
+# ---------------------------------------------------------------------------
+def test_powder_fp32_matches_oracle(eng, orc):
+    n = 2_000_000
+    desc = W.powder(n_histories=n)
+    gpu = gpu_run(eng, desc, n)
+    o = orc.OracleScene(desc).run(n)
+    m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
+    m2, e2 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    assert_totals(m1, e1, m2, e2)
+    # Bragg peaks appear where 2 theta = 2 asin(lambda / 2 d)
+    lines = W.fcc_bragg_lines()
+    d = np.asarray(lines["d"])
+    tt = np.degrees(2 * np.arcsin(1.5 / (2 * d[2 * d >= 1.5])))
+    bins = (tt / 0.05).astype(int)
+    bg = np.median(m1[200:3400])
+    assert all(m1[max(b - 3, 0):b + 4].max() > 3 * bg for b in bins)
+
+
+def test_powder_biased_equals_unbiased_on_gpu(eng):
+    n = 4_000_000
+    a = gpu_run(eng, W.powder(n_histories=n), n)["raw"]
+    b = gpu_run(eng, W.powder(n_histories=n, g=(1.0, 5.0, 5.0)), n, seed=777)["raw"]
+    m1, e1 = stats(a["sum"], a["sumsq"], n)
+    m2, e2 = stats(b["sum"], b["sumsq"], n)
+    keep = np.arange(m1.size) >= 40   # the direct beam at 0..2 deg is heavy-tailed when g > 1
+    ok, info = compare_tallies(m1[keep], e1[keep], m2[keep], e2[keep])
+    assert ok, info
+    assert_totals(m1, e1, m2, e2, rel=2e-3)
+
+
+# ---------------------------------------------------------------------------
+# Workload 3 (guide, FP32)
+# ---------------------------------------------------------------------------
+def test_guide_fp32_matches_oracle(eng, orc):
+    n = 1_000_000
+    desc = W.guide(n_histories=n)
+    gpu = gpu_run(eng, desc, n)
+    o = orc.OracleScene(desc).run(n)
+    m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
+    m2, e2 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    assert_totals(m1, e1, m2, e2)
+    assert gpu["counters"]["mirror_hits"] > 0
+
+
+def test_guide_fp64_histories_match_oracle(eng, orc):
+    n = 20_000
+    desc = W.guide(n_histories=n, precision="f64")
+    gpu = gpu_run(eng, desc, n, records=n)
+    o = orc.OracleScene(desc).run(n, records=True)
+    gr, orr = gpu["records"], o["records"]
+    same = gr["end"] == orr["end"]
+    assert same.mean() >= 0.999
+    ok = same & (orr["end"] == 2)
+    assert np.allclose(gr["w_final"][ok], orr["w_final"][ok], rtol=1e-9, atol=1e-300)
+    assert np.allclose(gr["final_pos"][ok], orr["final_pos"][ok], rtol=1e-9, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Workload 4 (batched + gradients)
+# ---------------------------------------------------------------------------
+def small_batched(n_inst=6, lo=2e4, hi=1e5, precision="f32"):
+    return W.batched(n_instances=n_inst, count_lo=lo, count_hi=hi, precision=precision)
+
+
+def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc):
+    desc = small_batched(n_inst=4, lo=3000, hi=8000, precision="f64")
+    sc = eng.Scene(desc)
+    sc.run(want_grad=True)
+    torch.cuda.synchronize()
+    osc = orc.OracleScene(desc)
+    for q in range(4):
+        n = int(desc["instances"]["counts"][q])
+        o = osc.run(n, inst=q, want_grad=True)
+        g = sc.raw(q)
+        assert np.allclose(g["sum"], o["sum"], rtol=1e-8, atol=1e-10), q
+        assert np.allclose(g["J"], o["J"], rtol=1e-7, atol=1e-8), q
+
+
+def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc):
+    desc = small_batched()
+    sc = eng.Scene(desc)
+    sc.run(want_grad=True)
+    torch.cuda.synchronize()
+    osc = orc.OracleScene(desc)
+    for q in (0, 3, 5):
+        n = int(desc["instances"]["counts"][q])
+        o = osc.run(n, inst=q, want_grad=True)
+        g = sc.raw(q)
+        m1, e1 = stats(g["sum"], g["sumsq"], n)
+        m2, e2 = stats(o["sum"], o["sumsq"], n)
+        ok, info = compare_tallies(m1, e1, m2, e2)
+        assert ok, (q, info)
+        for p in range(3):
+            j1, f1 = stats(g["J"][p], g["J2"][p], n)
+            j2, f2 = stats(o["J"][p], o["J2"][p], n)
+            assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
+
+
+def test_backward_contracts_gradient_tallies(eng):
+    desc = small_batched(n_inst=3, lo=5e4, hi=5e4)
+    sc = eng.Scene(desc)
+    sc.run(want_grad=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    grad = rng.normal(size=(3, sc.total_bins))
+    got = sc.backward(torch.tensor(grad, device="cuda")).cpu().numpy()
+    for q in range(3):
+        n = float(desc["instances"]["counts"][q])
+        J = sc.raw(q)["J"]
+        expect = (J @ grad[q]) / n
+        kinds = [p["kind"] for p in desc["params"]]
+        for p, k in enumerate(kinds):
+            if k != "radius":
+                expect[p] /= desc["instances"]["params"][q][p]
+        assert np.allclose(got[q], expect, rtol=1e-10, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Workload 5 (imaging, small scene)
+# ---------------------------------------------------------------------------
+def test_imaging_small_scene_matches_oracle(eng, orc):
+    n = 300_000
+    desc = W.imaging(n_histories=n, n_prims=60, psd_bins=32)
+    gpu = gpu_run(eng, desc, n, want_grad=True)
+    o = orc.OracleScene(desc).run(n, want_grad=True)
+    m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
+    m2, e2 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    assert_totals(m1, e1, m2, e2)
+    for p in range(3):
+        j1, f1 = stats(gpu["raw"]["J"][p], gpu["raw"]["J2"][p], n)
+        j2, f2 = stats(o["J"][p], o["J2"][p], n)
+        assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
