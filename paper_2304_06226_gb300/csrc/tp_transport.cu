@@ -97,6 +97,7 @@ struct Particle {
   int vol, nscat;
   uint32_t k, hid, inst, sub0, nsec;
   int secondary;
+  int last;  // primitive just left or reflected off (-1: none)
 };
 
 template <typename R>
@@ -255,9 +256,12 @@ __device__ R exit_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int*
   return best < R(0) ? R(0) : best;
 }
 
-// Distance to enter p from outside (inf if never); face id out.
+// Distance to enter p from outside (inf if never); face id out.  Pieces of the
+// solid along the ray that end before tmin are ignored: tmin > 0 is used for
+// the primitive just left, so that rounding at its surface cannot send the
+// neutron straight back in.
 template <typename R>
-__device__ R entry_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int* face) {
+__device__ R entry_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int* face, R tmin) {
   R q[3], v[3];
   to_local(p, x, u, q, v);
   const R INF = Tr<R>::inf();
@@ -278,7 +282,7 @@ __device__ R entry_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int
       if (ta > tn) { tn = ta; fn = fa; }
       if (tb < tf) tf = tb;
     }
-    if (tn > tf || tf <= R(0)) return INF;
+    if (tn > tf || tf <= tmin) return INF;
     *face = fn;
     return tn > R(0) ? tn : R(0);
   }
@@ -317,11 +321,11 @@ __device__ R entry_dist(const DPrim<R>& p, R dR, const R x[3], const R u[3], int
   int f = f0;
   if (z0 > a) { a = z0; f = fz0; }
   if (z1 < b) b = z1;
-  if (a < b && b > R(0)) { *face = f; return a > R(0) ? a : R(0); }
+  if (a < b && b > tmin) { *face = f; return a > R(0) ? a : R(0); }
   a = s1; b = e1; f = f1;
   if (z0 > a) { a = z0; f = fz0; }
   if (z1 < b) b = z1;
-  if (a < b && b > R(0)) { *face = f; return a > R(0) ? a : R(0); }
+  if (a < b && b > tmin) { *face = f; return a > R(0) ? a : R(0); }
   return INF;
 }
 
@@ -345,11 +349,14 @@ __device__ __forceinline__ R world_exit(const KParams<R>& kp, const R x[3], cons
   return exit_dist(w, R(0), x, u, &f);
 }
 
+// Point location: primitive containing x (skipping `skip`), -1 for the world
+// region, -2 outside the world.
 template <typename R>
-__device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3]) {
+__device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3],
+                                      int skip = -1) {
   if (!world_inside(kp, x)) return -2;
   for (int i = 0; i < kp.nprim; ++i)
-    if (inside(V.prims[i], dR, x)) return i;
+    if (i != skip && inside(V.prims[i], dR, x)) return i;
   return -1;
 }
 
@@ -505,7 +512,7 @@ __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R
   P.w = R(1);
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
-  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0;
+  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0; P.last = -1;
   if (kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
                           fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
     P.w = R(0);
@@ -589,6 +596,7 @@ __device__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle
   S->nscat = P.nscat + 1;
   S->sub0 = 4u + 2u * P.nsec;
   S->k = 0;
+  S->last = -1;
   P.nsec++;
   scatter_dir(V, mat, proc, P.lam, S->u, Tr<R>::u01(r.y), Tr<R>::u01(r.z), Tr<R>::u01(r.w));
   cnt[C_SEC]++;
@@ -631,9 +639,10 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
     db = exit_dist(V.prims[P.vol], dR, P.x, P.u, &face);
   } else {
     db = world_exit(kp, P.x, P.u);
+    const R tmin = R(2) * nudge_len(P.x);
     for (int i = 0; i < kp.nprim; ++i) {
       int f;
-      const R t = entry_dist(V.prims[i], dR, P.x, P.u, &f);
+      const R t = entry_dist(V.prims[i], dR, P.x, P.u, &f, i == P.last ? tmin : R(0));
       if (t < db) { db = t; target = i; face = f; }
     }
   }
@@ -659,7 +668,8 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
       if (pf.exit_mask) score<R, GRAD>(kp, V, P, (unsigned)pf.exit_mask, face);
       const R e = nudge_len(P.x);
       R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
-      const int v = locate(kp, V, dR, xn);
+      const int v = locate(kp, V, dR, xn, from);
+      P.last = from;
       if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
           ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
         R n[3];
@@ -700,6 +710,7 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
       if (!(Rf > R(0))) return END_MIRROR;
 #pragma unroll
       for (int i = 0; i < 3; ++i) P.u[i] -= R(2) * n[i] * un;
+      P.last = target;
       const R e = nudge_len(P.x);
 #pragma unroll
       for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
@@ -717,6 +728,7 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
 #pragma unroll
     for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
     P.vol = target;
+    P.last = -1;
     if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
     if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
     if (pt.role == TP_ROLE_BLACK) return END_BLACK;

@@ -134,7 +134,7 @@ class Scene:
                      None if fst is None else fst.ctypes.data_as(C.POINTER(C.c_uint64)),
                      int(want_grad), _stream_handle(stream), block_size, ctas_per_sm,
                      None if records is None else records.data_ptr(),
-                     0 if records is None else records.numel() // C.sizeof(N.tp_record))
+                     0 if records is None else records.numel() * records.element_size() // C.sizeof(N.tp_record))
         N.tp_run_histories(self.handle, r)
 
     def tally(self, t: int, instance: int = 0, device: bool = True):
