@@ -256,6 +256,42 @@ tp_status tp_get_launch(tp_scene* s, int* block_size, int* ctas_per_sm);
 /* Total bins over all tallies (per instance). */
 int tp_total_bins(const tp_scene* s);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free run (the paper has no counterpart: this is a deployment
+ * entry point of this library).
+ *
+ * Some callers cannot call cudaMalloc: code whose device memory is owned by
+ * another allocator, or that runs where new device allocations are not
+ * allowed.  tp_run_histories_noalloc runs the same transport kernel as
+ * tp_run_histories for a scene given as a description, without creating a
+ * scene and without allocating device or pinned host memory.  The scene
+ * tables, the per-run work description and the kernel's work counter, event
+ * counters and status word are kept in one fixed device array of
+ * TP_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library holds
+ * until the process exits.
+ *  - desc, mats[n_mats], bias ([n_mats][TP_NPROC], NULL = all 1) and r are
+ *    read as in tp_create_scene, tp_set_materials, tp_set_bias and
+ *    tp_run_histories; r->want_grad and r->records must be 0/NULL.
+ *  - sum, sumsq: caller-owned device arrays of [n_instances][total bins]
+ *    doubles; the call ADDS sum w and sum w^2 of every bin into them.
+ *  - counters_out (host, may be NULL): the counters of this call.
+ *  - Limits: at most TP_NOALLOC_MAX_INSTANCES instances and
+ *    TP_NOALLOC_MAX_TABLE_BYTES bytes of scene tables (checked first:
+ *    TP_ERR_INVALID_ARG with a message naming the limit).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - The call waits for its own work on r->stream before returning.  Every
+ *    call shares the one array, which keeps the last call's contents (each
+ *    call clears what must start at zero): calls that overlap on the GPU, from
+ *    several threads or streams, race and give wrong results. */
+#define TP_NOALLOC_MAX_INSTANCES 64
+#define TP_NOALLOC_MAX_TABLE_BYTES 65536
+#define TP_NOALLOC_SCRATCH_BYTES (65536 + 4096 + 256)
+tp_status tp_run_histories_noalloc(const tp_scene_desc* desc, const tp_material* mats, int n_mats,
+                                   const double* bias, const tp_run* r, double* sum, double* sumsq,
+                                   int64_t counters_out[8]);
+
 void tp_destroy_scene(tp_scene* s);
 const char* tp_last_error(void);
 

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -816,3 +817,208 @@ void tp_destroy_scene(tp_scene* s) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of tp_run_histories
+// ===========================================================================
+// For callers that cannot allocate device memory (code running where the device
+// memory is owned by another allocator, or where cudaMalloc is not allowed):
+// everything the transport kernel needs besides its inputs and outputs -- the
+// scene tables, the per-run work description and the work counter, event
+// counters and status word -- lives in one file-scope device array that every
+// GPU loading this library holds until the process exits.
+namespace {
+
+constexpr size_t kNaBlobBytes = TP_NOALLOC_MAX_TABLE_BYTES;
+constexpr size_t kNaWorkOff = kNaBlobBytes;                      // prefix, first ids, params
+constexpr size_t kNaWorkBytes = 4096;
+constexpr size_t kNaCtlOff = kNaWorkOff + kNaWorkBytes;         // work counter, counters, status
+constexpr size_t kNaCtlBytes = 256;
+static_assert(kNaCtlOff + kNaCtlBytes == TP_NOALLOC_SCRATCH_BYTES, "scratch layout");
+static_assert((TP_NOALLOC_MAX_INSTANCES + 1) * 8 + TP_NOALLOC_MAX_INSTANCES * 8 +
+                  TP_NOALLOC_MAX_INSTANCES * kMaxPar * 8 <= kNaWorkBytes, "work section");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kNaMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+tp_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  TP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) return fail(TP_ERR_INVALID_ARG, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    TP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return TP_OK;
+}
+
+}  // namespace
+
+extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_material* mats, int n_mats,
+                                              const double* bias, const tp_run* r, double* sum, double* sumsq,
+                                              int64_t counters_out[8]) {
+  g_err.clear();
+  if (!d || !r || !r->n_histories || !sum || !sumsq || (n_mats > 0 && !mats) || n_mats < 0)
+    return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (r->want_grad || r->records) return fail(TP_ERR_INVALID_ARG, "no gradients or records in the allocation-free call");
+  if (d->n_instances < 1 || d->n_instances > TP_NOALLOC_MAX_INSTANCES)
+    return fail(TP_ERR_INVALID_ARG, "n_instances %d: the allocation-free call takes 1..%d", d->n_instances,
+                TP_NOALLOC_MAX_INSTANCES);
+  if (d->precision != TP_FP32 && d->precision != TP_FP64) return fail(TP_ERR_INVALID_ARG, "precision %d", d->precision);
+  if (d->world_shape != TP_BOX && d->world_shape != TP_SPHERE) return fail(TP_ERR_INVALID_ARG, "world shape %d", d->world_shape);
+  if (!finite_all(d->world_centre, 3) || !finite_all(d->world_params, 3)) return fail(TP_ERR_INVALID_ARG, "world not finite");
+  if (d->world_shape == TP_BOX && !(d->world_params[0] > 0 && d->world_params[1] > 0 && d->world_params[2] > 0))
+    return fail(TP_ERR_INVALID_ARG, "world half extents must be positive");
+  if (d->world_shape == TP_SPHERE && !(d->world_params[1] > 0)) return fail(TP_ERR_INVALID_ARG, "world radius must be positive");
+  if (d->n_prims < 0 || (d->n_prims > 0 && !d->prims) || d->n_mirrors < 0 || (d->n_mirrors > 0 && !d->mirrors))
+    return fail(TP_ERR_INVALID_ARG, "prims / mirrors");
+  if (d->n_tallies < 0 || d->n_tallies > TP_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))
+    return fail(TP_ERR_INVALID_ARG, "n_tallies %d (max %d)", d->n_tallies, TP_MAX_TALLIES);
+  if (d->n_params < 0 || d->n_params > TP_MAX_PARAMS || (d->n_params > 0 && (!d->inst_params || !d->param_kind)))
+    return fail(TP_ERR_INVALID_ARG, "parameters");
+  if (d->event_cap < 0) return fail(TP_ERR_INVALID_ARG, "event_cap");
+
+  // host-side scene: the same checks and tables as tp_create_scene, no device memory
+  tp_scene s;
+  s.precision = d->precision;
+  s.event_cap = d->event_cap > 0 ? d->event_cap : 4096;
+  s.world_shape = d->world_shape;
+  for (int i = 0; i < 3; ++i) { s.world_c[i] = d->world_centre[i]; s.world_p[i] = d->world_params[i]; }
+  s.prims.assign(d->prims, d->prims + d->n_prims);
+  s.mirrors.assign(d->mirrors, d->mirrors + d->n_mirrors);
+  s.source = d->source;
+  s.tallies.assign(d->tallies, d->tallies + d->n_tallies);
+  s.n_inst = d->n_instances;
+  s.n_par = d->n_params;
+  s.param_kind.assign(d->param_kind, d->param_kind + d->n_params);
+  s.radius_nominal = d->radius_nominal;
+  s.inst_params.assign((size_t)s.n_inst * kMaxPar, 0.0);
+  for (int q = 0; q < s.n_inst; ++q)
+    for (int p = 0; p < s.n_par; ++p) {
+      if (s.param_kind[p] < TP_PAR_RADIUS || s.param_kind[p] > TP_PAR_DENSITY) return fail(TP_ERR_INVALID_ARG, "param_kind[%d]", p);
+      const double v = d->inst_params[(size_t)q * s.n_par + p];
+      if (!std::isfinite(v) || (s.param_kind[p] != TP_PAR_RADIUS && !(v > 0)))
+        return fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d]", q, p);
+      s.inst_params[(size_t)q * kMaxPar + p] = v;
+    }
+  for (int i = 0; i < d->n_prims; ++i) {
+    const tp_prim& p = s.prims[i];
+    if (p.shape < TP_BOX || p.shape > TP_SPHERE || p.axis < 0 || p.axis > 2 || p.role < TP_ROLE_BULK ||
+        p.role > TP_ROLE_BLACK || p.mirror < -1 || p.mirror >= d->n_mirrors || p.material < -1 ||
+        !finite_all(p.centre, 3) || !finite_all(p.params, 3))
+      return fail(TP_ERR_INVALID_ARG, "prim %d", i);
+    if (p.shape == TP_BOX && !(p.params[0] > 0 && p.params[1] > 0 && p.params[2] > 0))
+      return fail(TP_ERR_INVALID_ARG, "prim %d: box half extents must be positive", i);
+    if (p.shape == TP_TUBE && !(p.params[2] > 0)) return fail(TP_ERR_INVALID_ARG, "prim %d: tube half height", i);
+  }
+  for (int i = 0; i < d->n_mirrors; ++i) {
+    const tp_mirror& m = s.mirrors[i];
+    if (!(m.R0 >= 0 && m.Qc >= 0 && m.W > 0 && m.alpha >= 0 && m.m >= 0)) return fail(TP_ERR_INVALID_ARG, "mirror %d", i);
+  }
+  const tp_source& src = s.source;
+  if ((src.kind != TP_SRC_PENCIL && src.kind != TP_SRC_RECT) || !(src.lambda_lo > 0) ||
+      !(src.lambda_hi >= src.lambda_lo) || !std::isfinite(src.lambda_hi) ||
+      !(src.div[0] >= 0 && src.div[0] < 1.5 && src.div[1] >= 0 && src.div[1] < 1.5))
+    return fail(TP_ERR_INVALID_ARG, "source");
+  s.tally_off.resize(s.tallies.size() + 1);
+  long long tb = 0;
+  for (int t = 0; t < d->n_tallies; ++t) {
+    const tp_tally_desc& T = s.tallies[t];
+    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_WLX || (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) ||
+        T.volume < -1 || T.volume >= d->n_prims || (T.volume == -1 && T.trigger == TP_PTS_ENTRY) ||
+        T.nbins[0] < 1 || T.nbins[1] < 1 || (T.kind != TP_TALLY_COUNT && !(T.hi[0] > T.lo[0])) ||
+        ((T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) && !(T.hi[1] > T.lo[1])))
+      return fail(TP_ERR_INVALID_ARG, "tally %d", t);
+    s.tally_off[t] = (int)tb;
+    tb += (long long)T.nbins[0] * T.nbins[1];
+  }
+  if (tb > (1ll << 30)) return fail(TP_ERR_INVALID_ARG, "too many bins");
+  s.total_bins = (int)tb;
+  s.tally_off[s.tallies.size()] = (int)tb;
+  tp_status st = validate_geometry(&s);
+  if (st != TP_OK) return st;
+  st = tp_set_materials(&s, mats, n_mats);
+  if (st != TP_OK) return st;
+  if (bias)
+    for (int m = 0; m < n_mats; ++m)
+      if ((st = tp_set_bias(&s, m, bias + (size_t)m * TP_NPROC)) != TP_OK) return st;
+  std::vector<uint8_t> blob = s.precision == TP_FP64 ? build_blob<double>(&s) : build_blob<float>(&s);
+  if (blob.size() > kNaBlobBytes)
+    return fail(TP_ERR_INVALID_ARG, "scene tables need %zu bytes; the allocation-free call holds at most %zu",
+                blob.size(), kNaBlobBytes);
+  s.blob_bytes = (uint32_t)blob.size();
+  unsigned long long total = 0;
+  std::vector<unsigned long long> work((size_t)2 * s.n_inst + 1);
+  for (int i = 0; i < s.n_inst; ++i) {
+    const unsigned long long first = r->first_history ? r->first_history[i] : 0ull;
+    if (r->n_histories[i] > 0xffffffffull || first + r->n_histories[i] > 0x100000000ull)
+      return fail(TP_ERR_INVALID_ARG, "instance %d: history ids must stay below 2^32", i);
+    work[i] = total;
+    work[(size_t)s.n_inst + 1 + i] = first;
+    total += r->n_histories[i];
+  }
+  work[s.n_inst] = total;
+
+  unsigned char* base = nullptr;
+  if ((st = noalloc_scratch(&base)) != TP_OK) return st;
+  cudaStream_t strm = (cudaStream_t)r->stream;
+  s.d_blob = base;
+  s.d_prefix = reinterpret_cast<unsigned long long*>(base + kNaWorkOff);
+  s.d_first = s.d_prefix + (s.n_inst + 1);
+  s.d_params = reinterpret_cast<double*>(s.d_first + s.n_inst);
+  s.d_work = reinterpret_cast<unsigned long long*>(base + kNaCtlOff);
+  s.d_counters = s.d_work + 1;
+  s.d_status = reinterpret_cast<int*>(s.d_counters + kNumCounters);
+  s.d_sum = sum;
+  s.d_sumsq = sumsq;
+  // the array keeps the previous call's contents: clear the work counter,
+  // counters and status, then copy this call's tables in
+  TP_CUDA(cudaMemsetAsync(base + kNaCtlOff, 0, kNaCtlBytes, strm));
+  TP_CUDA(cudaMemcpyAsync(s.d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, strm));
+  TP_CUDA(cudaMemcpyAsync(s.d_prefix, work.data(), work.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, strm));
+  TP_CUDA(cudaMemcpyAsync(s.d_params, s.inst_params.data(), s.inst_params.size() * sizeof(double), cudaMemcpyHostToDevice, strm));
+  if (total > 0) {
+    int dev = 0, sms = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    TP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    s.sm_count = sms;
+    int block = 0, ctas = 0;
+    if ((st = pick_launch(&s, false, r->block_size, r->ctas_per_sm, &block, &ctas)) != TP_OK) return st;
+    const int grid = sms * ctas;
+    long long chunk = (long long)(total / (unsigned long long)((long long)grid * (block / 32) * 8));
+    chunk = std::max(1ll, std::min(256ll, chunk));
+    cudaError_t ce;
+    if (s.precision == TP_FP64) {
+      KParams<double> k{};
+      fill_common(&s, k);
+      k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
+      k.total = total; k.chunk = (int)chunk;
+      ce = launch_transport_f64(k, false, grid, block, smem_bytes(&s), strm);
+    } else {
+      KParams<float> k{};
+      fill_common(&s, k);
+      k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
+      k.total = total; k.chunk = (int)chunk;
+      ce = launch_transport_f32(k, false, grid, block, smem_bytes(&s), strm);
+    }
+    if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
+  }
+  // the host copies above read pageable memory that dies with this call
+  TP_CUDA(cudaStreamSynchronize(strm));
+  if (counters_out) {
+    unsigned long long h[kNumCounters];
+    int status = 0;
+    TP_CUDA(cudaMemcpy(h, s.d_counters, sizeof h, cudaMemcpyDeviceToHost));
+    TP_CUDA(cudaMemcpy(&status, s.d_status, sizeof status, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kNumCounters; ++i) counters_out[i] = (int64_t)h[i];
+    if (status != 0) return fail((tp_status)status, "a device-side wait gave up (status %d)", status);
+  }
+  return TP_OK;
+}

@@ -106,6 +106,9 @@ SIGNATURES = {
     "tp_total_bins": (C.c_int, [SCENE_P]),
     "tp_destroy_scene": (None, [SCENE_P]),
     "tp_last_error": (C.c_char_p, []),
+    "tp_run_histories_noalloc": (C.c_int, [C.POINTER(tp_scene_desc), C.POINTER(tp_material), C.c_int,
+                                           DP, C.POINTER(tp_run), C.c_void_p, C.c_void_p,
+                                           C.POINTER(C.c_int64)]),
 }
 
 
