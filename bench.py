@@ -139,7 +139,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
     # ---- warm-up (also JIT-free: the library is ahead-of-time compiled) ----
     for _ in range(args.warmup):
-        sc.run(n, first=first)
+        sc.run(n, first=first, kernel=args.kernel)
     torch.cuda.synchronize()
     sc.reset()
     if dist:
@@ -152,7 +152,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         for k in range(args.steps):
             flush_l2(flush)
             ev[k][0].record(stream)
-            sc.run(n, first=first, stream=stream)
+            sc.run(n, first=first, stream=stream, kernel=args.kernel)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -184,7 +184,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         sc.reset()
-        sc.run(n, first=first)
+        sc.run(n, first=first, kernel=args.kernel)
         for t in range(len(sc.tally_bins)):
             o = sc.tally_off[t]
             NN.tp_read_tallies(sc.handle, t, 0, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
@@ -211,7 +211,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "data": "synthetic",
         "config": workload_config(args.workload, label, {
             "histories_per_step_per_gpu": n, "tallies": "FP64 sum w, sum w^2 per bin",
-            "launch": {"block": sc.launch()[0], "ctas_per_sm": sc.launch()[1]},
+            "launch": dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch())),
             "parallelism": f"history ids sharded over {world} GPU(s)"}),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
@@ -327,6 +327,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powder")
     ap.add_argument("--histories", type=int, default=0, help="override the histories per step")
+    ap.add_argument("--kernel", type=int, default=0, help="0 autotuned, 1 history-based, 2 event-based")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batched-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

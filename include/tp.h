@@ -191,7 +191,11 @@ typedef struct {
  * the launch shape and runs over disjoint id ranges add up.
  * want_grad accumulates the score-function tallies for tp_backward.
  * stream: a cudaStream_t (NULL = legacy default stream).
- * block_size / ctas_per_sm: 0 = autotuned per scene.
+ * kernel: TP_KERNEL_HISTORY (one neutron per thread until it ends),
+ *   TP_KERNEL_EVENT (neutrons regrouped by event type every event in a
+ *   shared-memory bank), or 0: the autotuner times both (and block sizes) on
+ *   the scene's first run with and without gradients and keeps the faster.
+ * block_size / ctas_per_sm: 0 = autotuned / the most that fit on an SM.
  * records: device array of n_records tp_record, or NULL. */
 typedef struct {
   uint64_t seed;
@@ -203,7 +207,10 @@ typedef struct {
   int ctas_per_sm;
   tp_record* records;
   uint64_t n_records;
+  int kernel;
 } tp_run;
+
+enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2 };
 
 /* Runs histories and accumulates their scores into the scene's tallies
  * (sum w, sum w^2 per bin per instance, and the gradient tallies).  Returns
@@ -249,9 +256,9 @@ tp_status tp_reset_tallies(tp_scene* s);
  * secondaries.  Synchronises. */
 tp_status tp_get_counters(tp_scene* s, int64_t out[8]);
 
-/* Launch configuration the autotuner picked (or the forced one): block size and
+/* Launch configuration of the last run: kernel (TP_KERNEL_*), block size and
  * CTAs per SM. */
-tp_status tp_get_launch(tp_scene* s, int* block_size, int* ctas_per_sm);
+tp_status tp_get_launch(tp_scene* s, int* kernel, int* block_size, int* ctas_per_sm);
 
 /* Total bins over all tallies (per instance). */
 int tp_total_bins(const tp_scene* s);

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tp_internal.h"
@@ -76,7 +77,8 @@ struct tp_scene {
   uint8_t* d_blob = nullptr;
   size_t blob_cap = 0;
   uint32_t blob_bytes = 0;
-  uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_tallies = 0, off_line_d = 0, off_line_cum = 0;
+  uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_tallies = 0, off_line_d = 0, off_line_cum = 0,
+           off_nb = 0;
   bool blob_dirty = true;
   // tallies
   double *d_sum = nullptr, *d_sumsq = nullptr, *d_J = nullptr, *d_J2 = nullptr;
@@ -91,8 +93,9 @@ struct tp_scene {
   int* d_status = nullptr;
   cudaEvent_t stage_done = nullptr;
   bool stage_pending = false;
-  // launch configuration
-  int block = 0, ctas_per_sm = 0;
+  // launch configuration: last used, and the autotuned choice per gradient mode
+  int kernel = 0, block = 0, ctas_per_sm = 0;
+  int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0};
 };
 
 namespace {
@@ -252,12 +255,59 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 // ---------------------------------------------------------------------------
 // Device scene tables in precision R
 // ---------------------------------------------------------------------------
+// Bounding radius about the centre over every instance, with a margin, and
+// the lists of touching primitives (boxes grown by a tolerance intersect).
+void neighbours(const tp_scene* s, std::vector<double>& bound, std::vector<int>& off, std::vector<int>& cnt,
+                std::vector<int>& list) {
+  const int np = (int)s->prims.size();
+  bool moving = false;
+  for (const auto& p : s->prims) moving |= (p.bind_rmin || p.bind_rmax);
+  const int ninst = moving ? s->n_inst : 1;
+  bound.assign(np, 0.0);
+  std::vector<Box3> box(np);
+  for (int i = 0; i < np; ++i) {
+    for (int q = 0; q < ninst; ++q) {
+      const Box3 b = aabb(s, s->prims[i], q);
+      double r2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        const double h = std::max(std::fabs(b.hi[k] - s->prims[i].centre[k]), std::fabs(b.lo[k] - s->prims[i].centre[k]));
+        r2 += h * h;
+      }
+      bound[i] = std::max(bound[i], std::sqrt(r2));
+      if (q == 0) box[i] = b;
+      for (int k = 0; k < 3; ++k) { box[i].lo[k] = std::min(box[i].lo[k], b.lo[k]); box[i].hi[k] = std::max(box[i].hi[k], b.hi[k]); }
+    }
+    double scale = 1.0;
+    for (int k = 0; k < 3; ++k) scale = std::max(scale, std::fabs(s->prims[i].centre[k]));
+    bound[i] = bound[i] * (1.0 + 1e-5) + 1e-5 * scale;
+  }
+  off.assign(np, 0);
+  cnt.assign(np, 0);
+  list.clear();
+  for (int i = 0; i < np; ++i) {
+    off[i] = (int)list.size();
+    for (int j = 0; j < np; ++j) {
+      if (j == i) continue;
+      bool touch = true;
+      for (int k = 0; k < 3; ++k) {
+        const double tol = 1e-4 * std::max({1.0, std::fabs(box[i].lo[k]), std::fabs(box[i].hi[k])});
+        if (box[j].lo[k] > box[i].hi[k] + tol || box[j].hi[k] < box[i].lo[k] - tol) touch = false;
+      }
+      if (touch) list.push_back(j);
+    }
+    cnt[i] = (int)list.size() - off[i];
+  }
+}
+
 template <typename R>
 std::vector<uint8_t> build_blob(tp_scene* s) {
   const int np = (int)s->prims.size(), nm = (int)s->mats.size(), nmir = (int)s->mirrors.size(),
             nt = (int)s->tallies.size();
   int nl = 0;
   for (const auto& m : s->mats) nl += (int)m.d.size();
+  std::vector<double> bound;
+  std::vector<int> nb_off, nb_cnt, nb_list;
+  neighbours(s, bound, nb_off, nb_cnt, nb_list);
   size_t off = 0;
   s->off_prims = (uint32_t)off; off = align16(off + sizeof(DPrim<R>) * np);
   s->off_mats = (uint32_t)off; off = align16(off + sizeof(DMat<R>) * std::max(nm, 1));
@@ -265,7 +315,9 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
   s->off_tallies = (uint32_t)off; off = align16(off + sizeof(DTally<R>) * std::max(nt, 1));
   s->off_line_d = (uint32_t)off; off = align16(off + sizeof(R) * std::max(nl, 1));
   s->off_line_cum = (uint32_t)off; off = align16(off + sizeof(R) * (nl + std::max(nm, 1)));
+  s->off_nb = (uint32_t)off; off = align16(off + sizeof(int) * std::max<size_t>(nb_list.size(), 1));
   std::vector<uint8_t> blob(off, 0);
+  if (!nb_list.empty()) std::memcpy(blob.data() + s->off_nb, nb_list.data(), nb_list.size() * sizeof(int));
   auto* P = reinterpret_cast<DPrim<R>*>(blob.data() + s->off_prims);
   for (int i = 0; i < np; ++i) {
     const tp_prim& p = s->prims[i];
@@ -274,6 +326,9 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
     d.shape = p.shape; d.axis = p.axis; d.material = p.material; d.role = p.role;
     d.mirror = p.mirror; d.flags = (p.bind_rmin ? F_BIND_RMIN : 0) | (p.bind_rmax ? F_BIND_RMAX : 0);
     d.entry_mask = 0; d.exit_mask = 0;
+    d.bound_r = (R)bound[i];
+    d.nb_off = nb_off[i];
+    d.nb_cnt = nb_cnt[i];
     for (int t = 0; t < nt; ++t) {
       if (s->tallies[t].volume != i) continue;
       if (s->tallies[t].trigger == TP_PTS_ENTRY) d.entry_mask |= 1 << t;
@@ -354,6 +409,7 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.blob_bytes = s->blob_bytes;
   k.off_prims = s->off_prims; k.off_mats = s->off_mats; k.off_mirrors = s->off_mirrors;
   k.off_tallies = s->off_tallies; k.off_line_d = s->off_line_d; k.off_line_cum = s->off_line_cum;
+  k.off_nb = s->off_nb;
   k.stage_blob = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
   k.nprim = (int)s->prims.size();
   k.nmat = (int)s->mats.size();
@@ -400,13 +456,122 @@ size_t smem_bytes(const tp_scene* s) { return s->blob_bytes <= kMaxStagedBlob ? 
 
 tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* block, int* ctas) {
   int b = req_block > 0 ? req_block : (s->block > 0 ? s->block : 256);
-  if (b % 32 != 0 || b < 32 || b > 512) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 512]", b);
+  if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 256]", b);
   int occ = 0;
   TP_CUDA(occupancy_transport(s->precision, grad, b, smem_bytes(s), &occ));
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "block_size %d does not fit on an SM", b);
   int c = req_ctas > 0 ? std::min(req_ctas, occ) : occ;
   *block = b;
   *ctas = c;
+  return TP_OK;
+}
+
+struct LaunchCfg {
+  int kernel, block, ctas;
+};
+
+size_t smem_event(const tp_scene* s, bool grad, int block) {
+  return smem_bytes(s) + align16(event_bank_bytes(s->precision, grad, block));
+}
+
+// Completes a launch configuration (CTAs per SM from the occupancy).
+tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c) {
+  if (kernel == TP_KERNEL_EVENT) {
+    const int b = req_block > 0 ? req_block : 256;
+    if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d: need a multiple of 32 in [32, 256]", b);
+    int occ = 0;
+    TP_CUDA(occupancy_transport_ev(s->precision, grad, b, smem_event(s, grad, b), &occ));
+    if (occ < 1) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d does not fit on an SM", b);
+    *c = LaunchCfg{TP_KERNEL_EVENT, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ};
+    return TP_OK;
+  }
+  int b = 0, ct = 0;
+  tp_status st = pick_launch(s, grad, req_block, req_ctas, &b, &ct);
+  if (st != TP_OK) return st;
+  *c = LaunchCfg{TP_KERNEL_HISTORY, b, ct};
+  return TP_OK;
+}
+
+struct Outputs {
+  double *sum, *sumsq, *J, *J2;
+  unsigned long long* counters;
+};
+
+template <typename R>
+cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
+                       tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st) {
+  KParams<R> k{};
+  fill_common(s, k);
+  k.key0 = (uint32_t)(seed & 0xffffffffu);
+  k.key1 = (uint32_t)(seed >> 32);
+  k.total = total;
+  k.records = records;
+  k.n_records = records ? n_records : 0;
+  k.sum = o.sum; k.sumsq = o.sumsq; k.J = o.J; k.J2 = o.J2; k.counters = o.counters;
+  const int grid = s->sm_count * c.ctas;
+  const long long warps = (long long)grid * (c.block / 32);
+  k.chunk = (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
+  cudaError_t e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (c.kernel == TP_KERNEL_EVENT) {
+    const size_t sm = smem_event(s, grad, c.block);
+    if constexpr (std::is_same<R, double>::value) return launch_transport_ev_f64(k, grad, grid, c.block, sm, st);
+    else return launch_transport_ev_f32(k, grad, grid, c.block, sm, st);
+  }
+  if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, grad, grid, c.block, smem_bytes(s), st);
+  else return launch_transport_f32(k, grad, grid, c.block, smem_bytes(s), st);
+}
+
+cudaError_t launch_cfg(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
+                       tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st) {
+  if (s->precision == TP_FP64) return launch_one<double>(s, c, grad, seed, total, records, n_records, o, st);
+  return launch_one<float>(s, c, grad, seed, total, records, n_records, o, st);
+}
+
+// Times every candidate (kernel, block size) on up to 2^22 of this run's
+// histories, scoring into scratch tallies, and keeps the fastest.
+tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long total, cudaStream_t st) {
+  const unsigned long long trial = std::min(total, 1ull << 22);
+  const size_t nb = (size_t)s->n_inst * std::max(1, s->total_bins);
+  const size_t per = grad ? 2 + 2 * (size_t)s->n_par : 2;
+  double* scratch = nullptr;
+  unsigned long long* cnt = nullptr;
+  TP_CUDA(cudaMalloc(&scratch, per * nb * sizeof(double)));
+  cudaError_t ce = cudaMalloc(&cnt, kNumCounters * sizeof(unsigned long long));
+  if (ce != cudaSuccess) { cudaFree(scratch); return fail(TP_ERR_OOM, "autotune scratch"); }
+  Outputs o{scratch, scratch + nb, grad ? scratch + 2 * nb : nullptr,
+            grad ? scratch + (2 + s->n_par) * nb : nullptr, cnt};
+  const int cand[][2] = {{TP_KERNEL_EVENT, 256}, {TP_KERNEL_EVENT, 128}, {TP_KERNEL_HISTORY, 128},
+                         {TP_KERNEL_HISTORY, 256}};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  LaunchCfg pick{0, 0, 0};
+  tp_status result = TP_OK;
+  for (const auto& c : cand) {
+    LaunchCfg cfg;
+    if (resolve(s, grad, c[0], c[1], 0, &cfg) != TP_OK) continue;   // does not fit: skip
+    for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
+      cudaEventRecord(a, st);
+      ce = launch_cfg(s, cfg, grad, seed, trial, nullptr, 0, o, st);
+      cudaEventRecord(b, st);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(b);
+      if (ce != cudaSuccess) break;
+    }
+    if (ce != cudaSuccess) { result = fail(TP_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce)); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) { best = ms; pick = cfg; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(scratch);
+  cudaFree(cnt);
+  if (result != TP_OK) return result;
+  if (pick.kernel == 0) return fail(TP_ERR_INVALID_ARG, "no launch configuration fits");
+  s->tuned_kernel[grad] = pick.kernel;
+  s->tuned_block[grad] = pick.block;
   return TP_OK;
 }
 
@@ -648,7 +813,8 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   if (!s || !r || !r->n_histories) return fail(TP_ERR_INVALID_ARG, "null argument");
   if (!s->have_materials) return fail(TP_ERR_STATE, "tp_set_materials first");
   if (r->want_grad && s->n_par == 0) return fail(TP_ERR_INVALID_ARG, "want_grad without parameters");
-  if (r->records && s->precision != TP_FP64 && r->n_records > 0) { /* allowed in FP32 too */ }
+  if (r->kernel < TP_KERNEL_AUTO || r->kernel > TP_KERNEL_EVENT) return fail(TP_ERR_INVALID_ARG, "kernel %d", r->kernel);
+  const bool grad = r->want_grad != 0;
   cudaStream_t st = (cudaStream_t)r->stream;
   if (s->blob_dirty) {
     tp_status e = upload_blob(s);
@@ -670,39 +836,29 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   }
   s->h_stage[s->n_inst] = total;
   if (total == 0) return TP_OK;
-  int block = 0, ctas = 0;
-  tp_status e = pick_launch(s, r->want_grad != 0, r->block_size, r->ctas_per_sm, &block, &ctas);
-  if (e != TP_OK) return e;
   TP_CUDA(cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
   TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
   TP_CUDA(cudaEventRecord(s->stage_done, st));
   s->stage_pending = true;
-  TP_CUDA(cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st));
-  const int grid = s->sm_count * ctas;
-  const long long warps = (long long)grid * (block / 32);
-  long long chunk = (long long)(total / (unsigned long long)(warps * 8));
-  chunk = std::max(1ll, std::min(256ll, chunk));
-  const size_t smem = smem_bytes(s);
-  cudaError_t ce;
-  if (s->precision == TP_FP64) {
-    KParams<double> k{};
-    fill_common(s, k);
-    k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
-    k.total = total; k.chunk = (int)chunk;
-    k.records = r->records; k.n_records = r->records ? r->n_records : 0;
-    ce = launch_transport_f64(k, r->want_grad != 0, grid, block, smem, st);
-  } else {
-    KParams<float> k{};
-    fill_common(s, k);
-    k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
-    k.total = total; k.chunk = (int)chunk;
-    k.records = r->records; k.n_records = r->records ? r->n_records : 0;
-    ce = launch_transport_f32(k, r->want_grad != 0, grid, block, smem, st);
+  int kernel = r->kernel, block = r->block_size;
+  if (kernel == TP_KERNEL_AUTO) {
+    if (s->tuned_kernel[grad] == 0) {
+      tp_status e = autotune(s, grad, r->seed, total, st);
+      if (e != TP_OK) return e;
+    }
+    kernel = s->tuned_kernel[grad];
+    if (block == 0) block = s->tuned_block[grad];
   }
+  LaunchCfg cfg;
+  tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg);
+  if (e != TP_OK) return e;
+  Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
+  cudaError_t ce = launch_cfg(s, cfg, grad, r->seed, total, r->records, r->n_records, o, st);
   if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
   for (int i = 0; i < s->n_inst; ++i) s->n_done[i] += (double)r->n_histories[i];
-  s->block = block;
-  s->ctas_per_sm = ctas;
+  s->kernel = cfg.kernel;
+  s->block = cfg.block;
+  s->ctas_per_sm = cfg.ctas;
   return TP_OK;
 }
 
@@ -796,8 +952,9 @@ tp_status tp_get_counters(tp_scene* s, int64_t out[8]) {
   return TP_OK;
 }
 
-tp_status tp_get_launch(tp_scene* s, int* block, int* ctas) {
-  if (!s || !block || !ctas) return fail(TP_ERR_INVALID_ARG, "null argument");
+tp_status tp_get_launch(tp_scene* s, int* kernel, int* block, int* ctas) {
+  if (!s || !kernel || !block || !ctas) return fail(TP_ERR_INVALID_ARG, "null argument");
+  *kernel = s->kernel;
   *block = s->block;
   *ctas = s->ctas_per_sm;
   return TP_OK;

@@ -22,12 +22,17 @@ enum { F_BIND_RMIN = 1, F_BIND_RMAX = 2 };
 
 // One primitive as the kernels see it.  Lengths in the transport precision R.
 // entry_mask / exit_mask: bit t set if tally t listens to ENTRY / EXIT here.
+// bound_r: radius of a sphere about c containing the primitive for every
+// instance (with a margin).  nb_off / nb_cnt: the primitives that touch this one
+// (the only candidates for the volume entered when leaving it).
 template <typename R>
 struct alignas(16) DPrim {
   R c[3];
   R p[3];
+  R bound_r;
   int shape, axis, material, role;
   int mirror, flags, entry_mask, exit_mask;
+  int nb_off, nb_cnt;
 };
 
 // Material: cross sections, bias factors and the location of its Bragg table.
@@ -60,7 +65,7 @@ template <typename R>
 struct KParams {
   const uint8_t* blob;
   uint32_t blob_bytes;
-  uint32_t off_prims, off_mats, off_mirrors, off_tallies, off_line_d, off_line_cum;
+  uint32_t off_prims, off_mats, off_mirrors, off_tallies, off_line_d, off_line_cum, off_nb;
   int stage_blob;  // 1: copy the blob into shared memory
   int nprim, nmat, ntally, npar;
   int param_kind[kMaxPar];
@@ -102,6 +107,13 @@ cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, i
 cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
 cudaError_t occupancy_transport(int precision, bool grad, int block, size_t smem, int* ctas);
+// Event-based variant: shared memory = tables + event_bank_bytes(...).
+cudaError_t launch_transport_ev_f32(const KParams<float>& p, bool grad, int grid, int block,
+                                    size_t smem, cudaStream_t st);
+cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block,
+                                    size_t smem, cudaStream_t st);
+size_t event_bank_bytes(int precision, bool grad, int block);
+cudaError_t occupancy_transport_ev(int precision, bool grad, int block, size_t smem, int* ctas);
 cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
                          double* err, cudaStream_t st);
 cudaError_t launch_backward(const double* J, const double* grad_tallies, const double* scale,

@@ -108,6 +108,7 @@ struct View {
   const DTally<R>* tallies;
   const R* line_d;
   const R* line_cum;
+  const int* nb;
 };
 
 // ---------------------------------------------------------------------------
@@ -349,16 +350,37 @@ __device__ __forceinline__ R world_exit(const KParams<R>& kp, const R x[3], cons
   return exit_dist(w, R(0), x, u, &f);
 }
 
-// Point location: primitive containing x (skipping `skip`), -1 for the world
-// region, -2 outside the world.
+// Point location: primitive containing x, -1 for the world region, -2 outside
+// the world.
 template <typename R>
-__device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3],
-                                      int skip = -1) {
+__device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3]) {
   if (!world_inside(kp, x)) return -2;
   for (int i = 0; i < kp.nprim; ++i)
-    if (i != skip && inside(V.prims[i], dR, x)) return i;
+    if (inside(V.prims[i], dR, x)) return i;
   return -1;
 }
+
+// Location just after leaving primitive `from`: only the primitives touching it
+// can contain the point.
+template <typename R>
+__device__ __forceinline__ int locate_after(const KParams<R>& kp, const View<R>& V, R dR, const R x[3],
+                                            int from) {
+  if (!world_inside(kp, x)) return -2;
+  const DPrim<R>& pf = V.prims[from];
+  for (int k = 0; k < pf.nb_cnt; ++k) {
+    const int i = V.nb[pf.nb_off + k];
+    if (inside(V.prims[i], dR, x)) return i;
+  }
+  return -1;
+}
+
+// Leaving a primitive through a face of its convex hull (every box face, the
+// outer surface and caps of a tube, the outer surface of a sphere), a ray can
+// never meet that primitive again.
+__device__ __forceinline__ bool hull_face(int shape, int face) {
+  return shape == TP_BOX || face != 1;
+}
+constexpr int kLastHull = 0x40000000;   // flag in Particle::last: skip that primitive entirely
 
 template <typename R>
 __device__ __forceinline__ void normal(const DPrim<R>& p, const R x[3], int face, R n[3]) {
@@ -611,19 +633,32 @@ __device__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle
 }
 
 // ---------------------------------------------------------------------------
-// One event of one neutron.  Returns -1 while alive, else the end code.
-// spawn: set when a radius-derivative secondary was created into *S.
+// One event of one neutron, in three parts: advance (cross sections, biased
+// flight, next boundary, move and weight), then either cross (relocation at a
+// boundary) or collide (interaction).  Each returns -1 while the neutron
+// lives, else its end code; advance returns kOutCross / kOutColl instead.
 // ---------------------------------------------------------------------------
+constexpr int kOutCross = 100, kOutColl = 101;
+
+template <typename R>
+struct Adv {
+  uint4 r0;           // random numbers of this event (sub-stream 0)
+  R sig[TP_NPROC];    // true cross sections at the event (collisions only)
+  R sig_g;
+  int face, target;   // crossing: face id; target primitive, -3 = leaving the world
+};
+
 template <typename R, bool GRAD>
-__device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
-                    unsigned long long* cnt, Particle<R>* S, bool* spawn) {
+__device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+                       unsigned long long* cnt, Adv<R>& a) {
   const R INF = Tr<R>::inf();
   P.k += 1;
   if ((int)P.k > kp.event_cap) { cnt[C_TRUNC]++; return END_TRUNCATED; }
   cnt[C_EVENTS]++;
-  const uint4 r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
+  a.r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
   const int mat = P.vol >= 0 ? V.prims[P.vol].material : -1;
-  R sig[TP_NPROC] = {R(0), R(0), R(0)};
+  R* sig = a.sig;
+  sig[0] = sig[1] = sig[2] = R(0);
   R sig_t = R(0), sig_g = R(0);
   if (mat >= 0) {
     sigma(V, mat, ip, P.lam, sig);
@@ -631,7 +666,8 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
     sig_t = sig[0] + sig[1] + sig[2];
     sig_g = m.g[0] * sig[0] + m.g[1] * sig[1] + m.g[2] * sig[2];
   }
-  const R l = sig_g > R(0) ? -d_log(Tr<R>::u01(r0.x)) / sig_g : INF;
+  a.sig_g = sig_g;
+  const R l = sig_g > R(0) ? -d_log(Tr<R>::u01(a.r0.x)) / sig_g : INF;
   // next boundary
   R db;
   int target = -3, face = -1;
@@ -640,14 +676,26 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
   } else {
     db = world_exit(kp, P.x, P.u);
     const R tmin = R(2) * nudge_len(P.x);
+    const int last = P.last & ~kLastHull;
+    const bool last_hull = (P.last & kLastHull) != 0;
     for (int i = 0; i < kp.nprim; ++i) {
+      const DPrim<R>& pi = V.prims[i];
+      if (i == last && last_hull) continue;
+      // bounding sphere: skip if the ray misses it or moves away from outside it
+      const R q0 = P.x[0] - pi.c[0], q1 = P.x[1] - pi.c[1], q2 = P.x[2] - pi.c[2];
+      const R qu = q0 * P.u[0] + q1 * P.u[1] + q2 * P.u[2];
+      const R qq = q0 * q0 + q1 * q1 + q2 * q2;
+      const R rb2 = pi.bound_r * pi.bound_r;
+      if (qq > rb2 && (qu >= R(0) || qq - qu * qu > rb2)) continue;
       int f;
-      const R t = entry_dist(V.prims[i], dR, P.x, P.u, &f, i == P.last ? tmin : R(0));
+      const R t = entry_dist(pi, dR, P.x, P.u, &f, i == last ? tmin : R(0));
       if (t < db) { db = t; target = i; face = f; }
     }
   }
-  const bool cross = l >= db;
-  const R x = cross ? db : l;
+  a.face = face;
+  a.target = target;
+  const bool crossing = l >= db;
+  const R x = crossing ? db : l;
   if (!(x < INF)) { cnt[C_LOST]++; return END_LOST; }
 #pragma unroll
   for (int i = 0; i < 3; ++i) P.x[i] += x * P.u[i];
@@ -659,83 +707,96 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
       if (kp.param_kind[p] == TP_PAR_SCALE && m.scale_par == p) P.A[p] -= sig[TP_PROC_BRAGG] * x;
     }
   }
-  if (cross) {
-    cnt[C_CROSS]++;
-    if (P.vol >= 0) {
-      // leave the current primitive: EXIT scorers, then relocate
-      const int from = P.vol;
-      const DPrim<R>& pf = V.prims[from];
-      if (pf.exit_mask) score<R, GRAD>(kp, V, P, (unsigned)pf.exit_mask, face);
-      const R e = nudge_len(P.x);
-      R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
-      const int v = locate(kp, V, dR, xn, from);
-      P.last = from;
-      if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
-          ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
-        R n[3];
-        normal(pf, P.x, face, n);
-        const int mnext = v >= 0 ? V.prims[v].material : -1;
-        const int mi = face == 0 ? pf.material : mnext;
-        const int mo = face == 0 ? mnext : pf.material;
-        *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
-      }
-      P.x[0] = xn[0]; P.x[1] = xn[1]; P.x[2] = xn[2];
-      if (v == -2) {
-        if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
-        return END_ESCAPED;
-      }
-      P.vol = v;
-      if (v >= 0) {
-        const DPrim<R>& pt = V.prims[v];
-        if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, -1);
-        if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
-        if (pt.role == TP_ROLE_BLACK) return END_BLACK;
-      }
-      return -1;
+  return crossing ? kOutCross : kOutColl;
+}
+
+// Relocation at the boundary reached by advance (face / target of `a`).
+// spawn: set when a radius-derivative secondary was created into *S.
+template <typename R, bool GRAD>
+__device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+                     unsigned long long* cnt, int face, int target, Particle<R>* S, bool* spawn) {
+  cnt[C_CROSS]++;
+  if (P.vol >= 0) {
+    // leave the current primitive: EXIT scorers, then relocate
+    const int from = P.vol;
+    const DPrim<R>& pf = V.prims[from];
+    if (pf.exit_mask) score<R, GRAD>(kp, V, P, (unsigned)pf.exit_mask, face);
+    const R e = nudge_len(P.x);
+    R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
+    const int v = locate_after(kp, V, dR, xn, from);
+    P.last = from | (hull_face(pf.shape, face) ? kLastHull : 0);
+    if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
+        ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
+      R n[3];
+      normal(pf, P.x, face, n);
+      const int mnext = v >= 0 ? V.prims[v].material : -1;
+      const int mi = face == 0 ? pf.material : mnext;
+      const int mo = face == 0 ? mnext : pf.material;
+      *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
     }
-    if (target == -3) {
+    P.x[0] = xn[0]; P.x[1] = xn[1]; P.x[2] = xn[2];
+    if (v == -2) {
       if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
       return END_ESCAPED;
     }
-    const DPrim<R>& pt = V.prims[target];
-    if (pt.mirror >= 0) {
-      // supermirror: weight R(Q), specular reflection (Eq. eMirrowNewDir)
-      R n[3];
-      normal(pt, P.x, face, n);
-      const R un = P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2];
-      const R Q = Tr<R>::kFourPi * fabs(un) / P.lam;
-      const R Rf = mirror_R(V.mirrors[pt.mirror], Q);
-      cnt[C_MIRROR]++;
-      P.w *= Rf;
-      if (!(Rf > R(0))) return END_MIRROR;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) P.u[i] -= R(2) * n[i] * un;
-      P.last = target;
-      const R e = nudge_len(P.x);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
-      return -1;
+    P.vol = v;
+    if (v >= 0) {
+      const DPrim<R>& pt = V.prims[v];
+      if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, -1);
+      if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
+      if (pt.role == TP_ROLE_BLACK) return END_BLACK;
     }
-    if (GRAD && kp.radius_par >= 0 && !P.secondary && pt.shape != TP_BOX &&
-        ((face == 0 && (pt.flags & F_BIND_RMAX)) || (face == 1 && (pt.flags & F_BIND_RMIN)))) {
-      R n[3];
-      normal(pt, P.x, face, n);
-      const int mi = face == 0 ? pt.material : -1;
-      const int mo = face == 0 ? -1 : pt.material;
-      *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
-    }
+    return -1;
+  }
+  if (target == -3) {
+    if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
+    return END_ESCAPED;
+  }
+  const DPrim<R>& pt = V.prims[target];
+  if (pt.mirror >= 0) {
+    // supermirror: weight R(Q), specular reflection (Eq. eMirrowNewDir)
+    R n[3];
+    normal(pt, P.x, face, n);
+    const R un = P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2];
+    const R Q = Tr<R>::kFourPi * fabs(un) / P.lam;
+    const R Rf = mirror_R(V.mirrors[pt.mirror], Q);
+    cnt[C_MIRROR]++;
+    P.w *= Rf;
+    if (!(Rf > R(0))) return END_MIRROR;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P.u[i] -= R(2) * n[i] * un;
+    P.last = target | (hull_face(pt.shape, face) ? kLastHull : 0);
     const R e = nudge_len(P.x);
 #pragma unroll
     for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
-    P.vol = target;
-    P.last = -1;
-    if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
-    if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
-    if (pt.role == TP_ROLE_BLACK) return END_BLACK;
     return -1;
   }
-  // ---- interaction ----
+  if (GRAD && kp.radius_par >= 0 && !P.secondary && pt.shape != TP_BOX &&
+      ((face == 0 && (pt.flags & F_BIND_RMAX)) || (face == 1 && (pt.flags & F_BIND_RMIN)))) {
+    R n[3];
+    normal(pt, P.x, face, n);
+    const int mi = face == 0 ? pt.material : -1;
+    const int mo = face == 0 ? -1 : pt.material;
+    *spawn = radius_crossing<R>(kp, V, P, ip, dR, mi, mo, n, S, cnt);
+  }
+  const R e = nudge_len(P.x);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
+  P.vol = target;
+  P.last = -1;
+  if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
+  if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
+  if (pt.role == TP_ROLE_BLACK) return END_BLACK;
+  return -1;
+}
+
+// Interaction at the point reached by advance: process j with probability
+// g_j Sigma_j / Sigma_g, weight / g_j, then absorption or a new direction.
+template <typename R, bool GRAD>
+__device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, unsigned long long* cnt,
+                       const uint4 r0, const R sig[TP_NPROC], R sig_g) {
   cnt[C_COLL]++;
+  const int mat = V.prims[P.vol].material;
   if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid < kp.n_records) {
     tp_record* rc = kp.records + P.hid;
     rc->first_collision[0] = (double)P.x[0];
@@ -772,6 +833,31 @@ __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, cons
   }
   P.nscat++;
   return -1;
+}
+
+// Collision after a separate advance: the event's random numbers and cross
+// sections are recomputed from the neutron's state (event k is unchanged).
+template <typename R, bool GRAD>
+__device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
+                             unsigned long long* cnt) {
+  const uint4 r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
+  R sig[TP_NPROC];
+  const int mat = V.prims[P.vol].material;
+  sigma(V, mat, ip, P.lam, sig);
+  const DMat<R>& m = V.mats[mat];
+  const R sig_g = m.g[0] * sig[0] + m.g[1] * sig[1] + m.g[2] * sig[2];
+  return collide<R, GRAD>(kp, V, P, cnt, r0, sig, sig_g);
+}
+
+// One whole event (history-based kernel).
+template <typename R, bool GRAD>
+__device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+                    unsigned long long* cnt, Particle<R>* S, bool* spawn) {
+  Adv<R> a;
+  const int r = advance<R, GRAD>(kp, V, P, ip, dR, cnt, a);
+  if (r == kOutCross) return cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, S, spawn);
+  if (r == kOutColl) return collide<R, GRAD>(kp, V, P, cnt, a.r0, a.sig, a.sig_g);
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -830,7 +916,7 @@ __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& 
 }
 
 template <typename R, bool GRAD>
-__global__ void __launch_bounds__(512) k_transport(const __grid_constant__ KParams<R> kp) {
+__global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
   const uint8_t* base = kp.blob;
@@ -848,6 +934,7 @@ __global__ void __launch_bounds__(512) k_transport(const __grid_constant__ KPara
   V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
   V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
   V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
+  V.nb = reinterpret_cast<const int*>(base + kp.off_nb);
 
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -926,6 +1013,237 @@ __global__ void __launch_bounds__(512) k_transport(const __grid_constant__ KPara
   }
 }
 
+// ---------------------------------------------------------------------------
+// Event-based persistent kernel: a bank of neutrons in shared memory, one slot
+// per thread, regrouped every event by what each neutron needs next.  Every
+// iteration builds, with warp ballots, one queue per event type -- new history,
+// advance inside a primitive, advance in the world region, crossing out of a
+// primitive, crossing into one, collision -- and runs the queues one after
+// the other with consecutive threads taking consecutive entries, so that the
+// warps of a phase all run the same code.
+// ---------------------------------------------------------------------------
+enum { EV_EMPTY = 0, EV_ADV = 1, EV_XEXIT = 2, EV_XENT = 3, EV_COLL = 4 };
+enum { Q_EMPTY = 0, Q_ADVP, Q_ADVW, Q_XEXIT, Q_XENT, Q_COLL, kNumQ };
+
+// Append `slot` to queue q if `pred`; all lanes of the warp must call this.
+__device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pred, int slot) {
+  const unsigned m = __ballot_sync(kFull, pred);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(kFull, base, __ffs(m) - 1);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned short)slot;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst, R* ip, R* dR) {
+  const double* q = kp.inst_params + (size_t)inst * kMaxPar;
+#pragma unroll
+  for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)__ldg(q + i);
+  *dR = kp.radius_par >= 0 ? ip[kp.radius_par] - kp.radius_nominal : R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ int pend_of(int type, int face, int target) {
+  return type | ((face + 1) << 4) | ((target + 4) << 8);
+}
+
+template <typename R, bool GRAD>
+__global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__ KParams<R> kp) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bar;
+  __shared__ int qcount[kNumQ];
+  __shared__ unsigned long long claim_base;
+  __shared__ int claim_state;  // 0 work left, 1 exhausted
+  const int NB = blockDim.x;
+  const int tid = threadIdx.x;
+  const uint8_t* base = kp.blob;
+  uint32_t tab = 0;
+  if (kp.stage_blob) {
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
+      if (tid == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+      return;
+    }
+    base = smem;
+    tab = (kp.blob_bytes + 15u) & ~15u;
+  }
+  View<R> V;
+  V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
+  V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
+  V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
+  V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
+  V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
+  V.nb = reinterpret_cast<const int*>(base + kp.off_nb);
+  // bank layout after the tables
+  Particle<R>* bank = reinterpret_cast<Particle<R>*>(smem + tab);
+  Particle<R>* park = bank + NB;                      // parked primaries (gradient runs)
+  int* pend = reinterpret_cast<int*>(park + (GRAD ? NB : 0));
+  int* parked = pend + NB;
+  unsigned short* qlist = reinterpret_cast<unsigned short*>(parked + NB);  // [kNumQ][NB]
+
+  unsigned long long cnt[kNumCounters];
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+  pend[tid] = EV_EMPTY;
+  parked[tid] = 0;
+  if (tid == 0) claim_state = 0;
+  __syncthreads();
+
+  for (int iter = 0;; ++iter) {
+    // ---- classify ----
+    if (tid < kNumQ) qcount[tid] = 0;
+    __syncthreads();
+    {
+      const int pe = pend[tid];
+      const int ty = pe & 15;
+      q_push(qlist + Q_EMPTY * NB, &qcount[Q_EMPTY], ty == EV_EMPTY, tid);
+      bool inprim = false;
+      if (ty == EV_ADV) inprim = bank[tid].vol >= 0;
+      q_push(qlist + Q_ADVP * NB, &qcount[Q_ADVP], ty == EV_ADV && inprim, tid);
+      q_push(qlist + Q_ADVW * NB, &qcount[Q_ADVW], ty == EV_ADV && !inprim, tid);
+    }
+    __syncthreads();
+    // ---- refill empty slots with new histories ----
+    const int n_empty = qcount[Q_EMPTY];
+    if (tid == 0) {
+      claim_base = kp.total;
+      if (n_empty > 0 && claim_state == 0) {
+        const unsigned long long b = atomicAdd(kp.work_counter, (unsigned long long)n_empty);
+        claim_base = b;
+        if (b + n_empty >= kp.total) claim_state = 1;
+      }
+    }
+    __syncthreads();
+    {
+      bool born = false, inprim = false;
+      int slot = 0;
+      if (tid < n_empty) {
+        slot = qlist[Q_EMPTY * NB + tid];
+        const unsigned long long g = claim_base + tid;
+        if (g < kp.total) {
+          Particle<R> P;
+          int lo = 0, hi = kp.n_inst - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+          }
+          P.inst = (uint32_t)lo;
+          P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
+          R ip[kMaxPar], dR;
+          load_params(kp, P.inst, ip, &dR);
+          cnt[C_HIST]++;
+          int end = -1;
+          born = source(kp, V, P, dR, &end);
+          if (!born) {
+            if (end == END_LOST) cnt[C_LOST]++;
+            finish(kp, P, end);
+          } else {
+            inprim = P.vol >= 0;
+            bank[slot] = P;
+            pend[slot] = EV_ADV;
+          }
+        }
+      }
+      q_push(qlist + Q_ADVP * NB, &qcount[Q_ADVP], born && inprim, slot);
+      q_push(qlist + Q_ADVW * NB, &qcount[Q_ADVW], born && !inprim, slot);
+    }
+    __syncthreads();
+    const int n_advp = qcount[Q_ADVP], n_advw = qcount[Q_ADVW];
+    if (n_advp + n_advw == 0 && claim_state == 1) break;   // uniform: shared values
+    // ---- advance: inside primitives, then in the world region ----
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int n = pass == 0 ? n_advp : n_advw;
+      const unsigned short* L = qlist + (pass == 0 ? Q_ADVP : Q_ADVW) * NB;
+      int slot = 0, out = -1;
+      if (tid < n) {
+        slot = L[tid];
+        Particle<R> P = bank[slot];
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        Adv<R> a;
+        out = advance<R, GRAD>(kp, V, P, ip, dR, cnt, a);
+        if (out == kOutCross) {
+          pend[slot] = pend_of<R>(P.vol >= 0 ? EV_XEXIT : EV_XENT, a.face, a.target);
+        } else if (out == kOutColl) {
+          pend[slot] = EV_COLL;
+        } else {
+          finish(kp, P, out);
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        }
+        bank[slot] = P;
+      }
+      const bool is_cross = out == kOutCross;
+      const bool exitp = is_cross && (pend[slot] & 15) == EV_XEXIT;
+      q_push(qlist + Q_XEXIT * NB, &qcount[Q_XEXIT], tid < n && is_cross && exitp, slot);
+      q_push(qlist + Q_XENT * NB, &qcount[Q_XENT], tid < n && is_cross && !exitp, slot);
+      q_push(qlist + Q_COLL * NB, &qcount[Q_COLL], tid < n && out == kOutColl, slot);
+    }
+    __syncthreads();
+    // ---- crossings: out of primitives, then into primitives / world exit ----
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int n = qcount[pass == 0 ? Q_XEXIT : Q_XENT];
+      const unsigned short* L = qlist + (pass == 0 ? Q_XEXIT : Q_XENT) * NB;
+      if (tid < n) {
+        const int slot = L[tid];
+        Particle<R> P = bank[slot];
+        const int pe = pend[slot];
+        const int face = ((pe >> 4) & 15) - 1, target = (pe >> 8) - 4;
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        Particle<R> S;
+        bool spawn = false;
+        const int end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, face, target, &S, &spawn);
+        if (end >= 0) finish(kp, P, end);
+        if (GRAD && spawn) {
+          if (end < 0) { park[slot] = P; parked[slot] = 1; }
+          P = S;
+          pend[slot] = EV_ADV;
+        } else if (end >= 0) {
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        } else {
+          pend[slot] = EV_ADV;
+        }
+        bank[slot] = P;
+      }
+    }
+    // ---- collisions ----
+    {
+      const int n = qcount[Q_COLL];
+      if (tid < n) {
+        const int slot = qlist[Q_COLL * NB + tid];
+        Particle<R> P = bank[slot];
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
+        if (end >= 0) {
+          finish(kp, P, end);
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        } else {
+          pend[slot] = EV_ADV;
+        }
+        bank[slot] = P;
+      }
+    }
+    __syncthreads();
+  }
+  // ---- counters ----
+  const int lane = tid & 31;
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) {
+    unsigned long long v = cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0 && v) atomicAdd(kp.counters + i, v);
+  }
+}
+
 // mean and standard error per bin
 __global__ void k_stats(const double* __restrict__ sum, const double* __restrict__ sumsq, double n,
                         int nbins, double* __restrict__ mean, double* __restrict__ err) {
@@ -978,6 +1296,34 @@ cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, 
   if (grad) k_transport<double, true><<<grid, block, smem, st>>>(p);
   else k_transport<double, false><<<grid, block, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_transport_ev_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
+                                    cudaStream_t st) {
+  if (grad) k_transport_ev<float, true><<<grid, block, smem, st>>>(p);
+  else k_transport_ev<float, false><<<grid, block, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+                                    cudaStream_t st) {
+  if (grad) k_transport_ev<double, true><<<grid, block, smem, st>>>(p);
+  else k_transport_ev<double, false><<<grid, block, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+size_t event_bank_bytes(int precision, bool grad, int block) {
+  const size_t ps = precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
+  return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
+}
+
+cudaError_t occupancy_transport_ev(int precision, bool grad, int block, size_t smem, int* ctas) {
+  const void* fn;
+  if (precision == TP_FP64) fn = grad ? (const void*)k_transport_ev<double, true> : (const void*)k_transport_ev<double, false>;
+  else fn = grad ? (const void*)k_transport_ev<float, true> : (const void*)k_transport_ev<float, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
 }
 
 static cudaError_t set_smem(const void* fn, size_t smem) {

@@ -119,7 +119,8 @@ class Scene:
         N.tp_reset_tallies(self.handle)
 
     def run(self, n=None, seed: int | None = None, first=None, want_grad: bool = False, stream=None,
-            block_size: int = 0, ctas_per_sm: int = 0, records: torch.Tensor | None = None) -> None:
+            block_size: int = 0, ctas_per_sm: int = 0, records: torch.Tensor | None = None,
+            kernel: int = 0) -> None:
         """Queue histories on `stream` (default: torch's current stream).  n: per
         instance counts (int for one instance, array for many; default: the
         workload's counts)."""
@@ -134,7 +135,8 @@ class Scene:
                      None if fst is None else fst.ctypes.data_as(C.POINTER(C.c_uint64)),
                      int(want_grad), _stream_handle(stream), block_size, ctas_per_sm,
                      None if records is None else records.data_ptr(),
-                     0 if records is None else records.numel() * records.element_size() // C.sizeof(N.tp_record))
+                     0 if records is None else records.numel() * records.element_size() // C.sizeof(N.tp_record),
+                     kernel)
         N.tp_run_histories(self.handle, r)
 
     def tally(self, t: int, instance: int = 0, device: bool = True):
@@ -166,7 +168,8 @@ class Scene:
     def counters(self) -> dict:
         return N.tp_get_counters(self.handle)
 
-    def launch(self) -> tuple[int, int]:
+    def launch(self) -> tuple[int, int, int]:
+        """(kernel, block size, CTAs per SM) of the last run."""
         return N.tp_get_launch(self.handle)
 
     def means(self) -> torch.Tensor:

@@ -21,6 +21,7 @@ TP_PTS_ENTRY, TP_PTS_EXIT = 0, 1
 TP_PAR_RADIUS, TP_PAR_SCALE, TP_PAR_DENSITY = 0, 1, 2
 TP_SRC_PENCIL, TP_SRC_RECT = 0, 1
 TP_FP32, TP_FP64 = 0, 1
+TP_KERNEL_AUTO, TP_KERNEL_HISTORY, TP_KERNEL_EVENT = 0, 1, 2
 TP_MAX_PARAMS = 4
 TP_MAX_TALLIES = 16
 COUNTER_NAMES = ["histories", "events", "collisions", "crossings", "truncated", "lost", "mirror_hits",
@@ -83,7 +84,7 @@ class tp_run(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("n_histories", C.POINTER(C.c_uint64)),
                 ("first_history", C.POINTER(C.c_uint64)), ("want_grad", C.c_int),
                 ("stream", C.c_void_p), ("block_size", C.c_int), ("ctas_per_sm", C.c_int),
-                ("records", C.c_void_p), ("n_records", C.c_uint64)]
+                ("records", C.c_void_p), ("n_records", C.c_uint64), ("kernel", C.c_int)]
 
 
 SCENE_P = C.c_void_p
@@ -102,7 +103,7 @@ SIGNATURES = {
     "tp_set_params": (C.c_int, [SCENE_P, DP]),
     "tp_reset_tallies": (C.c_int, [SCENE_P]),
     "tp_get_counters": (C.c_int, [SCENE_P, C.POINTER(C.c_int64)]),
-    "tp_get_launch": (C.c_int, [SCENE_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tp_get_launch": (C.c_int, [SCENE_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tp_total_bins": (C.c_int, [SCENE_P]),
     "tp_destroy_scene": (None, [SCENE_P]),
     "tp_last_error": (C.c_char_p, []),
@@ -193,10 +194,10 @@ def tp_get_counters(scene: int) -> dict:
     return dict(zip(COUNTER_NAMES, list(out)))
 
 
-def tp_get_launch(scene: int) -> tuple[int, int]:
-    b, c = C.c_int(), C.c_int()
-    check(lib.tp_get_launch(scene, C.byref(b), C.byref(c)), "tp_get_launch")
-    return b.value, c.value
+def tp_get_launch(scene: int) -> tuple[int, int, int]:
+    k, b, c = C.c_int(), C.c_int(), C.c_int()
+    check(lib.tp_get_launch(scene, C.byref(k), C.byref(b), C.byref(c)), "tp_get_launch")
+    return k.value, b.value, c.value
 
 
 def tp_total_bins(scene: int) -> int:

@@ -46,6 +46,11 @@ def gpu_run(eng, desc, n, records=0, want_grad=False, seed=None, **kw):
     return out
 
 
+def sc_kernel_ok(gpu):
+    k, b, c = gpu["scene"].launch()
+    return k in (1, 2) and b > 0 and c > 0
+
+
 def assert_totals(m1, e1, m2, e2, rel=1e-3, nsig=4.0):
     t1, t2 = m1.sum(), m2.sum()
     s = math.sqrt((e1 ** 2).sum() + (e2 ** 2).sum())
@@ -55,11 +60,15 @@ def assert_totals(m1, e1, m2, e2, rel=1e-3, nsig=4.0):
 # ---------------------------------------------------------------------------
 # Workload 1 (slab, FP64): history by history
 # ---------------------------------------------------------------------------
+KERNELS = [1, 2]   # TP_KERNEL_HISTORY, TP_KERNEL_EVENT
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("g", [1.0, 3.0])
-def test_slab_fp64_histories_match_oracle(eng, orc, g):
+def test_slab_fp64_histories_match_oracle(eng, orc, g, kernel):
     n = 50_000
     desc = W.slab(g=g, n_histories=n, precision="f64")
-    gpu = gpu_run(eng, desc, n, records=n)
+    gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
     o = orc.OracleScene(desc).run(n, records=True)
     gr, orr = gpu["records"], o["records"]
     same_nan = np.isnan(gr["first_collision"][:, 0]) == np.isnan(orr["first_collision"][:, 0])
@@ -106,12 +115,13 @@ def test_slab_first_history_offset_and_split_runs_add_up(eng):
     assert np.allclose(parts["sumsq"], whole["sumsq"], rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("block,ctas", [(32, 1), (128, 0), (512, 0), (256, 1)])
-def test_launch_shape_does_not_change_results(eng, block, ctas):
+@pytest.mark.parametrize("kernel,block,ctas", [(1, 32, 1), (1, 128, 0), (1, 64, 0), (1, 256, 1),
+                                               (2, 32, 1), (2, 128, 0), (2, 256, 0), (2, 256, 1)])
+def test_launch_shape_does_not_change_results(eng, kernel, block, ctas):
     n = 30_011   # ragged against every chunk size
     desc = W.slab(g=3.0, n_histories=n, precision="f64")
-    ref = gpu_run(eng, desc, n)["raw"]
-    got = gpu_run(eng, desc, n, block_size=block, ctas_per_sm=ctas)["raw"]
+    ref = gpu_run(eng, desc, n, kernel=1)["raw"]
+    got = gpu_run(eng, desc, n, block_size=block, ctas_per_sm=ctas, kernel=kernel)["raw"]
     assert np.allclose(got["sum"], ref["sum"], rtol=1e-12, atol=1e-14)
 
 
@@ -130,10 +140,11 @@ def test_tiny_and_empty_runs(eng, orc, n):
 # ---------------------------------------------------------------------------
 # Workload 2 (powder, FP32)
 # ---------------------------------------------------------------------------
-def test_powder_fp32_matches_oracle(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_powder_fp32_matches_oracle(eng, orc, kernel):
     n = 2_000_000
     desc = W.powder(n_histories=n)
-    gpu = gpu_run(eng, desc, n)
+    gpu = gpu_run(eng, desc, n, kernel=kernel)
     o = orc.OracleScene(desc).run(n)
     m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
     m2, e2 = stats(o["sum"], o["sumsq"], n)
@@ -161,10 +172,11 @@ def test_powder_biased_equals_unbiased_on_gpu(eng):
     assert_totals(m1, e1, m2, e2, rel=2e-3)
 
 
-def test_powder_fp64_histories_match_oracle(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_powder_fp64_histories_match_oracle(eng, orc, kernel):
     n = 30_000
     desc = W.powder(n_histories=n, precision="f64")
-    gpu = gpu_run(eng, desc, n, records=n)
+    gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
     o = orc.OracleScene(desc).run(n, records=True)
     gr, orr = gpu["records"], o["records"]
     same = (gr["end"] == orr["end"]) & (gr["nscat"] == orr["nscat"]) & (gr["nevents"] == orr["nevents"])
@@ -189,6 +201,7 @@ def test_powder_full_size_in_bench_launch_shape(eng, orc):
     c = gpu["counters"]
     assert c["histories"] == n and c["lost"] == 0
     assert c["truncated"] == 0, c
+    assert sc_kernel_ok(gpu)
     o = orc.OracleScene(desc).run(nrec, records=True)
     gr, orr = gpu["records"], o["records"]
     same = (gr["end"] == orr["end"]) & (gr["nscat"] == orr["nscat"])
@@ -206,10 +219,11 @@ def test_powder_full_size_in_bench_launch_shape(eng, orc):
 # ---------------------------------------------------------------------------
 # Workload 3 (guide, FP32)
 # ---------------------------------------------------------------------------
-def test_guide_fp32_matches_oracle(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_guide_fp32_matches_oracle(eng, orc, kernel):
     n = 1_000_000
     desc = W.guide(n_histories=n)
-    gpu = gpu_run(eng, desc, n)
+    gpu = gpu_run(eng, desc, n, kernel=kernel)
     o = orc.OracleScene(desc).run(n)
     m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
     m2, e2 = stats(o["sum"], o["sumsq"], n)
@@ -219,10 +233,11 @@ def test_guide_fp32_matches_oracle(eng, orc):
     assert gpu["counters"]["mirror_hits"] > 0
 
 
-def test_guide_fp64_histories_match_oracle(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_guide_fp64_histories_match_oracle(eng, orc, kernel):
     n = 20_000
     desc = W.guide(n_histories=n, precision="f64")
-    gpu = gpu_run(eng, desc, n, records=n)
+    gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
     o = orc.OracleScene(desc).run(n, records=True)
     gr, orr = gpu["records"], o["records"]
     same = gr["end"] == orr["end"]
@@ -239,10 +254,11 @@ def small_batched(n_inst=6, lo=2e4, hi=1e5, precision="f32"):
     return W.batched(n_instances=n_inst, count_lo=lo, count_hi=hi, precision=precision)
 
 
-def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc, kernel):
     desc = small_batched(n_inst=4, lo=3000, hi=8000, precision="f64")
     sc = eng.Scene(desc)
-    sc.run(want_grad=True)
+    sc.run(want_grad=True, kernel=kernel)
     torch.cuda.synchronize()
     osc = orc.OracleScene(desc)
     for q in range(4):
@@ -253,10 +269,11 @@ def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc):
         assert np.allclose(g["J"], o["J"], rtol=1e-7, atol=1e-8), q
 
 
-def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc, kernel):
     desc = small_batched()
     sc = eng.Scene(desc)
-    sc.run(want_grad=True)
+    sc.run(want_grad=True, kernel=kernel)
     torch.cuda.synchronize()
     osc = orc.OracleScene(desc)
     for q in (0, 3, 5):
