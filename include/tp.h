@@ -174,7 +174,8 @@ tp_status tp_set_materials(tp_scene* s, const tp_material* m, int n);
 tp_status tp_set_bias(tp_scene* s, int material, const double g[TP_NPROC]);
 
 /* Optional per-history record (first collision, final state), written for
- * histories of instance 0 with history id < n_records. */
+ * the first n_records histories of instance 0 of a run: history id
+ * first_history[0] + i goes to records[i]. */
 typedef struct {
   double first_collision[3];
   double dir_after_first[3];

@@ -97,7 +97,7 @@ struct Particle {
   int vol, nscat;
   uint32_t k, hid, inst, sub0, nsec;
   int secondary;
-  int last;  // primitive just left or reflected off (-1: none)
+  int last;  // primitive just left, flags and stuck count (see kNoPrim)
 };
 
 template <typename R>
@@ -380,7 +380,17 @@ __device__ __forceinline__ int locate_after(const KParams<R>& kp, const View<R>&
 __device__ __forceinline__ bool hull_face(int shape, int face) {
   return shape == TP_BOX || face != 1;
 }
-constexpr int kLastHull = 0x40000000;   // flag in Particle::last: skip that primitive entirely
+// Particle::last packs the primitive just left (bits 0-23, kNoPrim = none),
+// a flag to skip it entirely (kLastHull), and the number of consecutive
+// boundary steps shorter than a few nudge lengths (bits 24-29): a neutron
+// caught between two surfaces that rounding makes overlap (an edge where two
+// mirror boxes meet, in FP32) is ended as lost after kMaxStuck of them.
+constexpr int kNoPrim = 0x00FFFFFF;
+constexpr int kPrimMask = 0x00FFFFFF;
+constexpr int kLastHull = 0x40000000;
+constexpr int kStuckShift = 24;
+constexpr int kStuckMask = 0x3F << kStuckShift;
+constexpr int kMaxStuck = 16;
 
 template <typename R>
 __device__ __forceinline__ void normal(const DPrim<R>& p, const R x[3], int face, R n[3]) {
@@ -534,7 +544,7 @@ __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R
   P.w = R(1);
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
-  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0; P.last = -1;
+  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0; P.last = kNoPrim;
   if (kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
                           fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
     P.w = R(0);
@@ -618,7 +628,7 @@ __device__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle
   S->nscat = P.nscat + 1;
   S->sub0 = 4u + 2u * P.nsec;
   S->k = 0;
-  S->last = -1;
+  S->last = kNoPrim;
   P.nsec++;
   scatter_dir(V, mat, proc, P.lam, S->u, Tr<R>::u01(r.y), Tr<R>::u01(r.z), Tr<R>::u01(r.w));
   cnt[C_SEC]++;
@@ -676,7 +686,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   } else {
     db = world_exit(kp, P.x, P.u);
     const R tmin = R(2) * nudge_len(P.x);
-    const int last = P.last & ~kLastHull;
+    const int last = P.last & kPrimMask;
     const bool last_hull = (P.last & kLastHull) != 0;
     for (int i = 0; i < kp.nprim; ++i) {
       const DPrim<R>& pi = V.prims[i];
@@ -697,6 +707,12 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   const bool crossing = l >= db;
   const R x = crossing ? db : l;
   if (!(x < INF)) { cnt[C_LOST]++; return END_LOST; }
+  {
+    int stuck = (P.last & kStuckMask) >> kStuckShift;
+    stuck = (crossing && db < R(4) * nudge_len(P.x)) ? stuck + 1 : 0;
+    if (stuck > kMaxStuck) { cnt[C_LOST]++; return END_LOST; }
+    P.last = (P.last & ~kStuckMask) | (stuck << kStuckShift);
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) P.x[i] += x * P.u[i];
   if (sig_g != sig_t) P.w *= d_exp((sig_g - sig_t) * x);
@@ -724,7 +740,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     const R e = nudge_len(P.x);
     R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
     const int v = locate_after(kp, V, dR, xn, from);
-    P.last = from | (hull_face(pf.shape, face) ? kLastHull : 0);
+    P.last = (P.last & kStuckMask) | from | (hull_face(pf.shape, face) ? kLastHull : 0);
     if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
         ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
       R n[3];
@@ -765,7 +781,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     if (!(Rf > R(0))) return END_MIRROR;
 #pragma unroll
     for (int i = 0; i < 3; ++i) P.u[i] -= R(2) * n[i] * un;
-    P.last = target | (hull_face(pt.shape, face) ? kLastHull : 0);
+    P.last = (P.last & kStuckMask) | target | (hull_face(pt.shape, face) ? kLastHull : 0);
     const R e = nudge_len(P.x);
 #pragma unroll
     for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
@@ -783,7 +799,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
 #pragma unroll
   for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
   P.vol = target;
-  P.last = -1;
+  P.last = (P.last & kStuckMask) | kNoPrim;
   if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
   if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
   if (pt.role == TP_ROLE_BLACK) return END_BLACK;
@@ -797,8 +813,8 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
                        const uint4 r0, const R sig[TP_NPROC], R sig_g) {
   cnt[C_COLL]++;
   const int mat = V.prims[P.vol].material;
-  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid < kp.n_records) {
-    tp_record* rc = kp.records + P.hid;
+  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+    tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->first_collision[0] = (double)P.x[0];
     rc->first_collision[1] = (double)P.x[1];
     rc->first_collision[2] = (double)P.x[2];
@@ -825,8 +841,8 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
     xline = Tr<R>::u01(r1.x);
   }
   scatter_dir(V, mat, j, P.lam, P.u, Tr<R>::u01(r0.z), Tr<R>::u01(r0.w), xline);
-  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid < kp.n_records) {
-    tp_record* rc = kp.records + P.hid;
+  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+    tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->dir_after_first[0] = (double)P.u[0];
     rc->dir_after_first[1] = (double)P.u[1];
     rc->dir_after_first[2] = (double)P.u[2];
@@ -902,8 +918,8 @@ __device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, u
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& P, int end) {
-  if (kp.records && !P.secondary && P.inst == 0 && P.hid < kp.n_records) {
-    tp_record* rc = kp.records + P.hid;
+  if (kp.records && !P.secondary && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+    tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->final_pos[0] = (double)P.x[0];
     rc->final_pos[1] = (double)P.x[1];
     rc->final_pos[2] = (double)P.x[2];
