@@ -30,10 +30,10 @@ sys.path.insert(0, str(ROOT))
 METRIC = "histories/s on 1 GB300: plain vs batched+adjoint, at matched tally error"
 UNIT = "histories/s"
 POWDER_N = 100_000_000
-# Thread instructions the transport kernel executes per powder history (ncu,
-# smsp__thread_inst_executed.sum / histories, on the 1e6-history powder case):
-# the per-unit figure of the ALU roofline.
-INST_PER_HISTORY = None
+# Thread instructions the history-based transport kernel executes per history
+# (ncu smsp__thread_inst_executed.sum / histories on the 2e6-history case of the
+# workload): the per-unit figure of the ALU-issue roofline.
+INST_PER_HISTORY = {"powder": 4092}
 SM_COUNT = 152
 LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -200,7 +200,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
     if rank != 0:
         return None
-    inst_ph = INST_PER_HISTORY.get(args.workload) if isinstance(INST_PER_HISTORY, dict) else None
+    # the per-unit figure was measured on the history-based kernel
+    inst_ph = INST_PER_HISTORY.get(args.workload) if sc.launch()[0] == 1 else None
     clocks = clk.summary()
     peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
     achieved = inst_ph * tot / (sum(kernel_ms) / 1e3) if inst_ph else None

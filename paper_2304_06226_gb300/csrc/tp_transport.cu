@@ -598,7 +598,7 @@ __device__ __forceinline__ void scatter_dir(const View<R>& V, int mat, int proc,
 // c = +Sigma_j,in, -Sigma_j,out over the scattering processes j.  Returns true
 // if a secondary was created in *S.
 template <typename R>
-__device__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
+__device__ __noinline__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
                                 R dR, int mi, int mo, const R n[3], Particle<R>* S,
                                 unsigned long long* cnt) {
   const R cosn = fabs(P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2]);
