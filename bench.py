@@ -48,7 +48,7 @@ def workload_desc(name: str):
     if name == "slab":
         return W.slab(g=3.0, n_histories=1_000_000), "slab, bias 3, 1e6 histories, FP64 transport"
     if name == "imaging":
-        return W.imaging(n_histories=100_000_000), "CSG imaging 1000 primitives, 1e8 histories"
+        return W.imaging(n_histories=1_000_000_000), "CSG imaging 1000 primitives, 512^2 PSD, 1e9 histories, FP32 transport"
     raise SystemExit(f"unknown workload {name}")
 
 

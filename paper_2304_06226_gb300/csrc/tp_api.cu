@@ -80,6 +80,11 @@ struct tp_scene {
   uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_tallies = 0, off_line_d = 0, off_line_cum = 0,
            off_nb = 0;
   bool blob_dirty = true;
+  // uniform grid (scenes with more than kGridMinPrims primitives)
+  int* d_grid = nullptr;   // [ncells + 1] starts, then items
+  int grid_n[3] = {0, 0, 0};
+  double grid_lo[3] = {0, 0, 0}, grid_hi[3] = {0, 0, 0};
+  int grid_cells = 0;
   // tallies
   double *d_sum = nullptr, *d_sumsq = nullptr, *d_J = nullptr, *d_J2 = nullptr;
   std::vector<double> n_done;  // histories run per instance
@@ -387,7 +392,85 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
   return blob;
 }
 
+constexpr int kGridMinPrims = 24;
+
+// Uniform grid over the bounding box of the primitives, about 8 cells per
+// primitive with cubic cells; each cell lists the primitives whose bounding box
+// (over every instance) meets it.
+tp_status upload_grid(tp_scene* s) {
+  if (s->d_grid) { cudaFree(s->d_grid); s->d_grid = nullptr; }
+  s->grid_cells = 0;
+  const int np = (int)s->prims.size();
+  if (np < kGridMinPrims) return TP_OK;
+  bool moving = false;
+  for (const auto& p : s->prims) moving |= (p.bind_rmin || p.bind_rmax);
+  const int ninst = moving ? s->n_inst : 1;
+  std::vector<Box3> box(np);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < np; ++i) {
+    box[i] = aabb(s, s->prims[i], 0);
+    for (int q = 1; q < ninst; ++q) {
+      const Box3 b = aabb(s, s->prims[i], q);
+      for (int k = 0; k < 3; ++k) { box[i].lo[k] = std::min(box[i].lo[k], b.lo[k]); box[i].hi[k] = std::max(box[i].hi[k], b.hi[k]); }
+    }
+    for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], box[i].lo[k]); hi[k] = std::max(hi[k], box[i].hi[k]); }
+  }
+  double vol = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    const double pad = 1e-4 * std::max(1.0, hi[k] - lo[k]);
+    lo[k] -= pad; hi[k] += pad;
+    vol *= hi[k] - lo[k];
+  }
+  const double h = std::cbrt(vol / (8.0 * np));
+  // pad every box by a small fraction of a cell so that rounding at cell faces
+  // during the walk cannot skip a primitive
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < 3; ++k) { box[i].lo[k] -= 1e-3 * h; box[i].hi[k] += 1e-3 * h; }
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    s->grid_n[k] = (int)std::max(1.0, std::min(256.0, std::round((hi[k] - lo[k]) / h)));
+    ncell *= s->grid_n[k];
+    s->grid_lo[k] = lo[k];
+    s->grid_hi[k] = hi[k];
+  }
+  std::vector<int> count(ncell + 1, 0);
+  auto range = [&](const Box3& b, int k, int* a0, int* a1) {
+    const double inv = s->grid_n[k] / (s->grid_hi[k] - s->grid_lo[k]);
+    *a0 = std::max(0, std::min(s->grid_n[k] - 1, (int)std::floor((b.lo[k] - s->grid_lo[k]) * inv)));
+    *a1 = std::max(0, std::min(s->grid_n[k] - 1, (int)std::floor((b.hi[k] - s->grid_lo[k]) * inv)));
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> fill;
+    if (pass == 1) {
+      for (long long c = 0; c < ncell; ++c) count[c + 1] += count[c];
+      fill.assign(count.begin(), count.end() - 1);
+    }
+    std::vector<int> items(pass == 1 ? count[ncell] : 0);
+    for (int i = 0; i < np; ++i) {
+      int r[3][2];
+      for (int k = 0; k < 3; ++k) range(box[i], k, &r[k][0], &r[k][1]);
+      for (int a = r[0][0]; a <= r[0][1]; ++a)
+        for (int b = r[1][0]; b <= r[1][1]; ++b)
+          for (int c = r[2][0]; c <= r[2][1]; ++c) {
+            const long long cell = ((long long)a * s->grid_n[1] + b) * s->grid_n[2] + c;
+            if (pass == 0) count[cell + 1]++;
+            else items[fill[cell]++] = i;
+          }
+    }
+    if (pass == 1) {
+      std::vector<int> all(count.begin(), count.end());
+      all.insert(all.end(), items.begin(), items.end());
+      TP_CUDA(cudaMalloc(&s->d_grid, all.size() * sizeof(int)));
+      TP_CUDA(cudaMemcpy(s->d_grid, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
+  s->grid_cells = (int)ncell;
+  return TP_OK;
+}
+
 tp_status upload_blob(tp_scene* s) {
+  tp_status gst = upload_grid(s);
+  if (gst != TP_OK) return gst;
   std::vector<uint8_t> blob = s->precision == TP_FP64 ? build_blob<double>(s) : build_blob<float>(s);
   if (blob.size() > s->blob_cap) {
     if (s->d_blob) cudaFree(s->d_blob);
@@ -441,6 +524,16 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.src_lam_lo = (R)src.lambda_lo;
   k.src_lam_hi = (R)src.lambda_hi;
   k.event_cap = s->event_cap;
+  k.use_grid = s->grid_cells > 0 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    k.grid_n[i] = s->grid_n[i];
+    k.grid_lo[i] = (R)s->grid_lo[i];
+    k.grid_hi[i] = (R)s->grid_hi[i];
+    k.grid_cell[i] = s->grid_n[i] > 0 ? (R)((s->grid_hi[i] - s->grid_lo[i]) / s->grid_n[i]) : R(1);
+    k.grid_inv[i] = s->grid_n[i] > 0 ? (R)(s->grid_n[i] / (s->grid_hi[i] - s->grid_lo[i])) : R(0);
+  }
+  k.grid_start = s->d_grid;
+  k.grid_items = s->d_grid ? s->d_grid + s->grid_cells + 1 : nullptr;
   k.n_inst = s->n_inst;
   k.inst_prefix = s->d_prefix;
   k.inst_first = s->d_first;
@@ -790,6 +883,7 @@ tp_status tp_set_params(tp_scene* s, const double* inst_params) {
   }
   TP_CUDA(cudaDeviceSynchronize());
   TP_CUDA(cudaMemcpy(s->d_params, s->inst_params.data(), s->inst_params.size() * sizeof(double), cudaMemcpyHostToDevice));
+  s->blob_dirty = true;   // bounding radii and neighbour lists depend on the radii
   return TP_OK;
 }
 
@@ -964,6 +1058,7 @@ void tp_destroy_scene(tp_scene* s) {
   if (!s) return;
   if (s->stage_pending) cudaEventSynchronize(s->stage_done);
   cudaFree(s->d_blob);
+  cudaFree(s->d_grid);
   cudaFree(s->d_sum); cudaFree(s->d_sumsq); cudaFree(s->d_J); cudaFree(s->d_J2);
   cudaFree(s->d_prefix); cudaFree(s->d_first); cudaFree(s->d_params); cudaFree(s->d_aux);
   cudaFree(s->d_work); cudaFree(s->d_counters); cudaFree(s->d_status);

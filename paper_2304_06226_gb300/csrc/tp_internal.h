@@ -78,6 +78,13 @@ struct KParams {
   // source
   int src_kind, src_aperture;
   R src_c[3], src_half[2], src_lam_lo, src_lam_hi, src_div[2], src_ap[2];
+  // uniform grid over the primitives (large scenes): cell (i,j,k) lists the
+  // primitives whose bounding box meets it, in CSR form (grid_start / grid_items)
+  int use_grid;
+  int grid_n[3];
+  R grid_lo[3], grid_hi[3], grid_cell[3], grid_inv[3];
+  const int* grid_start;
+  const int* grid_items;
   // random numbers
   uint32_t key0, key1;
   int event_cap;

@@ -355,6 +355,20 @@ __device__ __forceinline__ R world_exit(const KParams<R>& kp, const R x[3], cons
 template <typename R>
 __device__ __forceinline__ int locate(const KParams<R>& kp, const View<R>& V, R dR, const R x[3]) {
   if (!world_inside(kp, x)) return -2;
+  if (kp.use_grid) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!(x[a] >= kp.grid_lo[a] && x[a] <= kp.grid_hi[a])) return -1;   // outside every primitive
+      c[a] = min(kp.grid_n[a] - 1, max(0, (int)floor((x[a] - kp.grid_lo[a]) * kp.grid_inv[a])));
+    }
+    const int cell = (c[0] * kp.grid_n[1] + c[1]) * kp.grid_n[2] + c[2];
+    for (int k = kp.grid_start[cell]; k < kp.grid_start[cell + 1]; ++k) {
+      const int i = kp.grid_items[k];
+      if (inside(V.prims[i], dR, x)) return i;
+    }
+    return -1;
+  }
   for (int i = 0; i < kp.nprim; ++i)
     if (inside(V.prims[i], dR, x)) return i;
   return -1;
@@ -688,18 +702,71 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
     const R tmin = R(2) * nudge_len(P.x);
     const int last = P.last & kPrimMask;
     const bool last_hull = (P.last & kLastHull) != 0;
-    for (int i = 0; i < kp.nprim; ++i) {
+    auto test = [&](int i) {
       const DPrim<R>& pi = V.prims[i];
-      if (i == last && last_hull) continue;
+      if (i == last && last_hull) return;
       // bounding sphere: skip if the ray misses it or moves away from outside it
       const R q0 = P.x[0] - pi.c[0], q1 = P.x[1] - pi.c[1], q2 = P.x[2] - pi.c[2];
       const R qu = q0 * P.u[0] + q1 * P.u[1] + q2 * P.u[2];
       const R qq = q0 * q0 + q1 * q1 + q2 * q2;
       const R rb2 = pi.bound_r * pi.bound_r;
-      if (qq > rb2 && (qu >= R(0) || qq - qu * qu > rb2)) continue;
+      if (qq > rb2 && (qu >= R(0) || qq - qu * qu > rb2)) return;
       int f;
       const R t = entry_dist(pi, dR, P.x, P.u, &f, i == last ? tmin : R(0));
       if (t < db) { db = t; target = i; face = f; }
+    };
+    if (kp.use_grid) {
+      // 3-D DDA through the cells the ray crosses, nearest first; stop once the
+      // best hit lies inside the cells already visited
+      R t0 = R(0), t1 = db;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (P.u[a] != R(0)) {
+          const R inv = R(1) / P.u[a];
+          R ta = (kp.grid_lo[a] - P.x[a]) * inv, tb = (kp.grid_hi[a] - P.x[a]) * inv;
+          if (ta > tb) { const R t = ta; ta = tb; tb = t; }
+          t0 = fmax(t0, ta);
+          t1 = fmin(t1, tb);
+        } else if (!(P.x[a] >= kp.grid_lo[a] && P.x[a] <= kp.grid_hi[a])) {
+          t1 = R(-1);
+        }
+      }
+      if (t0 <= t1) {
+        int c[3], stp[3];
+        R tnext[3], tdel[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R pa = P.x[a] + t0 * P.u[a];
+          c[a] = min(kp.grid_n[a] - 1, max(0, (int)floor((pa - kp.grid_lo[a]) * kp.grid_inv[a])));
+          if (P.u[a] > R(0)) {
+            stp[a] = 1;
+            tnext[a] = (kp.grid_lo[a] + (c[a] + 1) * kp.grid_cell[a] - P.x[a]) / P.u[a];
+            tdel[a] = kp.grid_cell[a] / P.u[a];
+          } else if (P.u[a] < R(0)) {
+            stp[a] = -1;
+            tnext[a] = (kp.grid_lo[a] + c[a] * kp.grid_cell[a] - P.x[a]) / P.u[a];
+            tdel[a] = -kp.grid_cell[a] / P.u[a];
+          } else {
+            stp[a] = 0;
+            tnext[a] = Tr<R>::inf();
+            tdel[a] = Tr<R>::inf();
+          }
+        }
+        const int maxsteps = kp.grid_n[0] + kp.grid_n[1] + kp.grid_n[2] + 3;
+        for (int it = 0; it < maxsteps; ++it) {
+          const int cell = (c[0] * kp.grid_n[1] + c[1]) * kp.grid_n[2] + c[2];
+          const int k1 = kp.grid_start[cell + 1];
+          for (int k = kp.grid_start[cell]; k < k1; ++k) test(kp.grid_items[k]);
+          const int a = (tnext[0] <= tnext[1]) ? (tnext[0] <= tnext[2] ? 0 : 2) : (tnext[1] <= tnext[2] ? 1 : 2);
+          const R texit = tnext[a];
+          if (db <= texit || texit >= t1) break;
+          c[a] += stp[a];
+          if (c[a] < 0 || c[a] >= kp.grid_n[a]) break;
+          tnext[a] += tdel[a];
+        }
+      }
+    } else {
+      for (int i = 0; i < kp.nprim; ++i) test(i);
     }
   }
   a.face = face;

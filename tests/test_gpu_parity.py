@@ -326,3 +326,34 @@ def test_imaging_small_scene_matches_oracle(eng, orc):
         j1, f1 = stats(gpu["raw"]["J"][p], gpu["raw"]["J2"][p], n)
         j2, f2 = stats(o["J"][p], o["J2"][p], n)
         assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_imaging_1000_primitives_fp64_histories_match_brute_force_oracle(eng, orc, kernel):
+    """The GPU walks a uniform grid; the oracle tests every primitive."""
+    n = 40_000
+    desc = W.imaging(n_histories=n, precision="f64", psd_bins=64)
+    gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
+    o = orc.OracleScene(desc).run(n, records=True)
+    gr, orr = gpu["records"], o["records"]
+    same = (gr["end"] == orr["end"]) & (gr["nscat"] == orr["nscat"]) & (gr["nevents"] == orr["nevents"])
+    assert same.mean() >= 0.9999, same.mean()
+    assert np.allclose(gr["final_pos"][same], orr["final_pos"][same], rtol=1e-9, atol=1e-9)
+    assert np.allclose(gr["w_final"][same], orr["w_final"][same], rtol=1e-9, atol=1e-300)
+    assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-7, atol=1e-10)
+
+
+def test_imaging_1000_primitives_fp32_statistics(eng, orc):
+    n = 400_000
+    desc = W.imaging(n_histories=n, psd_bins=16)
+    gpu = gpu_run(eng, desc, n, want_grad=True)
+    o = orc.OracleScene(desc).run(n, want_grad=True)
+    m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
+    m2, e2 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    assert_totals(m1, e1, m2, e2)
+    for p in range(3):
+        j1, f1 = stats(gpu["raw"]["J"][p], gpu["raw"]["J2"][p], n)
+        j2, f2 = stats(o["J"][p], o["J2"][p], n)
+        assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
