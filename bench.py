@@ -248,7 +248,7 @@ def run_batched(args, W, Scene, torch) -> dict:
     stream = torch.cuda.current_stream()
     grad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda")
     for _ in range(max(1, args.warmup // 2)):
-        sc.run(want_grad=True)
+        sc.run(want_grad=True, graph=True)
     torch.cuda.synchronize()
     sc.reset()
     steps = max(1, args.batched_steps)
@@ -256,7 +256,7 @@ def run_batched(args, W, Scene, torch) -> dict:
     fw_ms, bw_ms = [], []
     for _ in range(steps):
         a.record(stream)
-        sc.run(want_grad=True, stream=stream)
+        sc.run(want_grad=True, stream=stream, graph=True)   # one persistent launch, replayed from a CUDA graph
         b.record(stream)
         sc.backward(grad, stream=stream)
         c.record(stream)

@@ -197,6 +197,11 @@ typedef struct {
  *   shared-memory bank), or 0: the autotuner times both (and block sizes) on
  *   the scene's first run with and without gradients and keeps the faster.
  * block_size / ctas_per_sm: 0 = autotuned / the most that fit on an SM.
+ * use_graph: 1 = run as a CUDA graph [work-description copies, work-counter
+ *   reset, persistent kernel] captured on the first call with a given launch
+ *   (kernel, block, CTAs, gradients, seed, total histories, records) and
+ *   replayed afterwards; history counts and first ids may change between
+ *   replays (they are read from the scene's pinned staging buffer).
  * records: device array of n_records tp_record, or NULL. */
 typedef struct {
   uint64_t seed;
@@ -209,6 +214,7 @@ typedef struct {
   tp_record* records;
   uint64_t n_records;
   int kernel;
+  int use_graph;
 } tp_run;
 
 enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2 };

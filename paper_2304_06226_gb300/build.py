@@ -15,7 +15,12 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libtp.so"
 OBJDIR = PKG / "_build"
-SOURCES = ["tp_transport.cu", "tp_api.cu"]
+# (source, object, extra flags): the transport kernels are compiled once per
+# precision so that the halves build in parallel
+UNITS = [("tp_transport.cu", "tp_transport_f32.o", ["-DTP_BUILD_F32"]),
+         ("tp_transport.cu", "tp_transport_f64.o", ["-DTP_BUILD_F64"]),
+         ("tp_api.cu", "tp_api.o", [])]
+SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,10 +48,10 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         flags += ["-Xptxas", "-v"]
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = OBJDIR / (Path(src).stem + ".o")
+    for src, objname, extra in UNITS:
+        obj = OBJDIR / objname
         objs.append(obj)
-        procs.append((src, subprocess.Popen([nvcc(), *flags, "-c", str(CSRC / src), "-o", str(obj)],
+        procs.append((src, subprocess.Popen([nvcc(), *flags, *extra, "-c", str(CSRC / src), "-o", str(obj)],
                                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     for src, p in procs:
         out, _ = p.communicate()

@@ -101,6 +101,10 @@ struct tp_scene {
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0};
+  // CUDA graph of the last graph run and the launch it was captured for
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  unsigned long long graph_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -551,7 +555,7 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
   int b = req_block > 0 ? req_block : (s->block > 0 ? s->block : 256);
   if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 256]", b);
   int occ = 0;
-  TP_CUDA(occupancy_transport(s->precision, grad, b, smem_bytes(s), &occ));
+  TP_CUDA(occupancy_transport(s->precision, grad, s->grid_cells > 0, b, smem_bytes(s), &occ));
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "block_size %d does not fit on an SM", b);
   int c = req_ctas > 0 ? std::min(req_ctas, occ) : occ;
   *block = b;
@@ -573,7 +577,7 @@ tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_cta
     const int b = req_block > 0 ? req_block : 256;
     if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d: need a multiple of 32 in [32, 256]", b);
     int occ = 0;
-    TP_CUDA(occupancy_transport_ev(s->precision, grad, b, smem_event(s, grad, b), &occ));
+    TP_CUDA(occupancy_transport_ev(s->precision, grad, s->grid_cells > 0, b, smem_event(s, grad, b), &occ));
     if (occ < 1) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d does not fit on an SM", b);
     *c = LaunchCfg{TP_KERNEL_EVENT, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ};
     return TP_OK;
@@ -665,6 +669,40 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   if (pick.kernel == 0) return fail(TP_ERR_INVALID_ARG, "no launch configuration fits");
   s->tuned_kernel[grad] = pick.kernel;
   s->tuned_block[grad] = pick.block;
+  return TP_OK;
+}
+
+// Runs [work-description copies, work-counter reset, kernel] as a CUDA graph,
+// captured on a private stream the first time a launch key is seen and
+// replayed on `st` afterwards.  The copies read the pinned staging buffer at
+// replay time, so counts and first ids may change between replays.
+tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* r, unsigned long long total,
+                    const Outputs& o, cudaStream_t st) {
+  const unsigned long long key[8] = {(unsigned long long)cfg.kernel, (unsigned long long)cfg.block,
+                                     (unsigned long long)cfg.ctas, (unsigned long long)grad, r->seed, total,
+                                     (unsigned long long)(uintptr_t)r->records, r->records ? r->n_records : 0};
+  if (!s->graph || std::memcmp(key, s->graph_key, sizeof key) != 0) {
+    if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+    if (!s->capture_stream) TP_CUDA(cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = s->capture_stream;
+    TP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long),
+                                     cudaMemcpyHostToDevice, cs);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, cs);
+    if (ce == cudaSuccess) ce = launch_cfg(s, cfg, grad, r->seed, total, r->records, r->n_records, o, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { s->graph = nullptr; return fail(TP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce)); }
+    std::memcpy(s->graph_key, key, sizeof key);
+  }
+  TP_CUDA(cudaGraphLaunch(s->graph, st));
+  TP_CUDA(cudaEventRecord(s->stage_done, st));
+  s->stage_pending = true;
   return TP_OK;
 }
 
@@ -930,13 +968,12 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   }
   s->h_stage[s->n_inst] = total;
   if (total == 0) return TP_OK;
-  TP_CUDA(cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
-  TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
-  TP_CUDA(cudaEventRecord(s->stage_done, st));
-  s->stage_pending = true;
   int kernel = r->kernel, block = r->block_size;
   if (kernel == TP_KERNEL_AUTO) {
     if (s->tuned_kernel[grad] == 0) {
+      // the trials read this run's work description
+      TP_CUDA(cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+      TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
       tp_status e = autotune(s, grad, r->seed, total, st);
       if (e != TP_OK) return e;
     }
@@ -947,8 +984,17 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg);
   if (e != TP_OK) return e;
   Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
-  cudaError_t ce = launch_cfg(s, cfg, grad, r->seed, total, r->records, r->n_records, o, st);
-  if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
+  if (r->use_graph) {
+    e = run_graph(s, cfg, grad, r, total, o, st);
+    if (e != TP_OK) return e;
+  } else {
+    TP_CUDA(cudaMemcpyAsync(s->d_prefix, s->h_stage, (s->n_inst + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    TP_CUDA(cudaEventRecord(s->stage_done, st));
+    s->stage_pending = true;
+    cudaError_t ce = launch_cfg(s, cfg, grad, r->seed, total, r->records, r->n_records, o, st);
+    if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
+  }
   for (int i = 0; i < s->n_inst; ++i) s->n_done[i] += (double)r->n_histories[i];
   s->kernel = cfg.kernel;
   s->block = cfg.block;
@@ -1057,6 +1103,8 @@ tp_status tp_get_launch(tp_scene* s, int* kernel, int* block, int* ctas) {
 void tp_destroy_scene(tp_scene* s) {
   if (!s) return;
   if (s->stage_pending) cudaEventSynchronize(s->stage_done);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
   cudaFree(s->d_blob);
   cudaFree(s->d_grid);
   cudaFree(s->d_sum); cudaFree(s->d_sumsq); cudaFree(s->d_J); cudaFree(s->d_J2);

@@ -664,6 +664,88 @@ __device__ __noinline__ bool radius_crossing(const KParams<R>& kp, const View<R>
 // ---------------------------------------------------------------------------
 constexpr int kOutCross = 100, kOutColl = 101;
 
+// Entry test of primitive i from the world region, with the bounding-sphere
+// early-out and the rules for the primitive just left; keeps the nearest.
+template <typename R>
+__device__ __forceinline__ void entry_test(const View<R>& V, R dR, const R x[3], const R u[3], int i, int last,
+                                           bool last_hull, R tmin, R* db, int* target, int* face) {
+  const DPrim<R>& pi = V.prims[i];
+  if (i == last && last_hull) return;
+  // bounding sphere: skip if the ray misses it or moves away from outside it
+  const R q0 = x[0] - pi.c[0], q1 = x[1] - pi.c[1], q2 = x[2] - pi.c[2];
+  const R qu = q0 * u[0] + q1 * u[1] + q2 * u[2];
+  const R qq = q0 * q0 + q1 * q1 + q2 * q2;
+  const R rb2 = pi.bound_r * pi.bound_r;
+  if (qq > rb2 && (qu >= R(0) || qq - qu * qu > rb2)) return;
+  int f;
+  const R t = entry_dist(pi, dR, x, u, &f, i == last ? tmin : R(0));
+  if (t < *db) { *db = t; *target = i; *face = f; }
+}
+
+// World-region search through the uniform grid: a 3-D DDA over the cells the
+// ray crosses, nearest first, stopping once the best hit lies inside the cells
+// already visited.  Out of line so that scenes without a grid keep a smaller
+// hot loop.
+template <typename R>
+__device__ __forceinline__ void grid_search(const KParams<R>& kp, const View<R>& V, R dR, R x0, R x1, R x2, R u0,
+                                         R u1, R u2, int last, bool last_hull, R tmin, R* db_io, int* target_io,
+                                         int* face_io) {
+  const R x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+  R db = *db_io;
+  int target = *target_io, face = *face_io;
+  R t0 = R(0), t1 = db;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (u[a] != R(0)) {
+      const R inv = R(1) / u[a];
+      R ta = (kp.grid_lo[a] - x[a]) * inv, tb = (kp.grid_hi[a] - x[a]) * inv;
+      if (ta > tb) { const R t = ta; ta = tb; tb = t; }
+      t0 = fmax(t0, ta);
+      t1 = fmin(t1, tb);
+    } else if (!(x[a] >= kp.grid_lo[a] && x[a] <= kp.grid_hi[a])) {
+      t1 = R(-1);
+    }
+  }
+  if (t0 <= t1) {
+    int c[3], stp[3];
+    R tnext[3], tdel[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R pa = x[a] + t0 * u[a];
+      c[a] = min(kp.grid_n[a] - 1, max(0, (int)floor((pa - kp.grid_lo[a]) * kp.grid_inv[a])));
+      if (u[a] > R(0)) {
+        stp[a] = 1;
+        tnext[a] = (kp.grid_lo[a] + (c[a] + 1) * kp.grid_cell[a] - x[a]) / u[a];
+        tdel[a] = kp.grid_cell[a] / u[a];
+      } else if (u[a] < R(0)) {
+        stp[a] = -1;
+        tnext[a] = (kp.grid_lo[a] + c[a] * kp.grid_cell[a] - x[a]) / u[a];
+        tdel[a] = -kp.grid_cell[a] / u[a];
+      } else {
+        stp[a] = 0;
+        tnext[a] = Tr<R>::inf();
+        tdel[a] = Tr<R>::inf();
+      }
+    }
+    const int maxsteps = kp.grid_n[0] + kp.grid_n[1] + kp.grid_n[2] + 3;
+    for (int it = 0; it < maxsteps; ++it) {
+      const int cell = (c[0] * kp.grid_n[1] + c[1]) * kp.grid_n[2] + c[2];
+      const int k1 = kp.grid_start[cell + 1];
+      for (int k = kp.grid_start[cell]; k < k1; ++k)
+        entry_test(V, dR, x, u, kp.grid_items[k], last, last_hull, tmin, &db, &target, &face);
+      const int a = (tnext[0] <= tnext[1]) ? (tnext[0] <= tnext[2] ? 0 : 2) : (tnext[1] <= tnext[2] ? 1 : 2);
+      const R texit = tnext[a];
+      if (db <= texit || texit >= t1) break;
+      c[a] += stp[a];
+      if (c[a] < 0 || c[a] >= kp.grid_n[a]) break;
+      tnext[a] += tdel[a];
+    }
+  }
+  *db_io = db;
+  *target_io = target;
+  *face_io = face;
+}
+
 template <typename R>
 struct Adv {
   uint4 r0;           // random numbers of this event (sub-stream 0)
@@ -672,7 +754,7 @@ struct Adv {
   int face, target;   // crossing: face id; target primitive, -3 = leaving the world
 };
 
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, bool GRID>
 __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
                        unsigned long long* cnt, Adv<R>& a) {
   const R INF = Tr<R>::inf();
@@ -702,71 +784,12 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
     const R tmin = R(2) * nudge_len(P.x);
     const int last = P.last & kPrimMask;
     const bool last_hull = (P.last & kLastHull) != 0;
-    auto test = [&](int i) {
-      const DPrim<R>& pi = V.prims[i];
-      if (i == last && last_hull) return;
-      // bounding sphere: skip if the ray misses it or moves away from outside it
-      const R q0 = P.x[0] - pi.c[0], q1 = P.x[1] - pi.c[1], q2 = P.x[2] - pi.c[2];
-      const R qu = q0 * P.u[0] + q1 * P.u[1] + q2 * P.u[2];
-      const R qq = q0 * q0 + q1 * q1 + q2 * q2;
-      const R rb2 = pi.bound_r * pi.bound_r;
-      if (qq > rb2 && (qu >= R(0) || qq - qu * qu > rb2)) return;
-      int f;
-      const R t = entry_dist(pi, dR, P.x, P.u, &f, i == last ? tmin : R(0));
-      if (t < db) { db = t; target = i; face = f; }
-    };
-    if (kp.use_grid) {
-      // 3-D DDA through the cells the ray crosses, nearest first; stop once the
-      // best hit lies inside the cells already visited
-      R t0 = R(0), t1 = db;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (P.u[a] != R(0)) {
-          const R inv = R(1) / P.u[a];
-          R ta = (kp.grid_lo[a] - P.x[a]) * inv, tb = (kp.grid_hi[a] - P.x[a]) * inv;
-          if (ta > tb) { const R t = ta; ta = tb; tb = t; }
-          t0 = fmax(t0, ta);
-          t1 = fmin(t1, tb);
-        } else if (!(P.x[a] >= kp.grid_lo[a] && P.x[a] <= kp.grid_hi[a])) {
-          t1 = R(-1);
-        }
-      }
-      if (t0 <= t1) {
-        int c[3], stp[3];
-        R tnext[3], tdel[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const R pa = P.x[a] + t0 * P.u[a];
-          c[a] = min(kp.grid_n[a] - 1, max(0, (int)floor((pa - kp.grid_lo[a]) * kp.grid_inv[a])));
-          if (P.u[a] > R(0)) {
-            stp[a] = 1;
-            tnext[a] = (kp.grid_lo[a] + (c[a] + 1) * kp.grid_cell[a] - P.x[a]) / P.u[a];
-            tdel[a] = kp.grid_cell[a] / P.u[a];
-          } else if (P.u[a] < R(0)) {
-            stp[a] = -1;
-            tnext[a] = (kp.grid_lo[a] + c[a] * kp.grid_cell[a] - P.x[a]) / P.u[a];
-            tdel[a] = -kp.grid_cell[a] / P.u[a];
-          } else {
-            stp[a] = 0;
-            tnext[a] = Tr<R>::inf();
-            tdel[a] = Tr<R>::inf();
-          }
-        }
-        const int maxsteps = kp.grid_n[0] + kp.grid_n[1] + kp.grid_n[2] + 3;
-        for (int it = 0; it < maxsteps; ++it) {
-          const int cell = (c[0] * kp.grid_n[1] + c[1]) * kp.grid_n[2] + c[2];
-          const int k1 = kp.grid_start[cell + 1];
-          for (int k = kp.grid_start[cell]; k < k1; ++k) test(kp.grid_items[k]);
-          const int a = (tnext[0] <= tnext[1]) ? (tnext[0] <= tnext[2] ? 0 : 2) : (tnext[1] <= tnext[2] ? 1 : 2);
-          const R texit = tnext[a];
-          if (db <= texit || texit >= t1) break;
-          c[a] += stp[a];
-          if (c[a] < 0 || c[a] >= kp.grid_n[a]) break;
-          tnext[a] += tdel[a];
-        }
-      }
+    if constexpr (GRID) {
+      grid_search(kp, V, dR, P.x[0], P.x[1], P.x[2], P.u[0], P.u[1], P.u[2], last, last_hull, tmin, &db,
+                  &target, &face);
     } else {
-      for (int i = 0; i < kp.nprim; ++i) test(i);
+      for (int i = 0; i < kp.nprim; ++i)
+        entry_test(V, dR, P.x, P.u, i, last, last_hull, tmin, &db, &target, &face);
     }
   }
   a.face = face;
@@ -933,11 +956,11 @@ __device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>
 }
 
 // One whole event (history-based kernel).
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, bool GRID>
 __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
                     unsigned long long* cnt, Particle<R>* S, bool* spawn) {
   Adv<R> a;
-  const int r = advance<R, GRAD>(kp, V, P, ip, dR, cnt, a);
+  const int r = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
   if (r == kOutCross) return cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, S, spawn);
   if (r == kOutColl) return collide<R, GRAD>(kp, V, P, cnt, a.r0, a.sig, a.sig_g);
   return r;
@@ -998,7 +1021,7 @@ __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& 
   }
 }
 
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, bool GRID>
 __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
@@ -1075,7 +1098,7 @@ __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KP
     if (__all_sync(kFull, done)) break;
     if (alive) {
       bool spawn = false;
-      const int end = step<R, GRAD>(kp, V, P, ip, dR, cnt, &S, &spawn);
+      const int end = step<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, &S, &spawn);
       if (end >= 0) finish(kp, P, end);
       if (GRAD && spawn) {
         if (end < 0) { park = P; parked = true; }
@@ -1132,7 +1155,7 @@ __device__ __forceinline__ int pend_of(int type, int face, int target) {
   return type | ((face + 1) << 4) | ((target + 4) << 8);
 }
 
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, bool GRID>
 __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
@@ -1247,7 +1270,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
         R ip[kMaxPar], dR;
         load_params(kp, P.inst, ip, &dR);
         Adv<R> a;
-        out = advance<R, GRAD>(kp, V, P, ip, dR, cnt, a);
+        out = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
         if (out == kOutCross) {
           pend[slot] = pend_of<R>(P.vol >= 0 ? EV_XEXIT : EV_XENT, a.face, a.target);
         } else if (out == kOutColl) {
@@ -1365,34 +1388,53 @@ __global__ void k_backward(const double* __restrict__ J, const double* __restric
   }
 }
 
-}  // namespace
+// kernel pointer for (precision, variant, gradients, grid)
+template <typename R>
+const void* transport_fn(bool ev, bool grad, bool grid) {
+  if (ev) {
+    if (grad) return grid ? (const void*)k_transport_ev<R, true, true> : (const void*)k_transport_ev<R, true, false>;
+    return grid ? (const void*)k_transport_ev<R, false, true> : (const void*)k_transport_ev<R, false, false>;
+  }
+  if (grad) return grid ? (const void*)k_transport<R, true, true> : (const void*)k_transport<R, true, false>;
+  return grid ? (const void*)k_transport<R, false, true> : (const void*)k_transport<R, false, false>;
+}
 
-cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
-                                 cudaStream_t st) {
-  if (grad) k_transport<float, true><<<grid, block, smem, st>>>(p);
-  else k_transport<float, false><<<grid, block, smem, st>>>(p);
+template <typename R>
+cudaError_t launch_any(const KParams<R>& p, bool ev, bool grad, int grid, int block, size_t smem, cudaStream_t st) {
+  const bool g = p.use_grid != 0;
+  if (ev) {
+    if (grad) { if (g) k_transport_ev<R, true, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, true, false><<<grid, block, smem, st>>>(p); }
+    else { if (g) k_transport_ev<R, false, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, false, false><<<grid, block, smem, st>>>(p); }
+  } else {
+    if (grad) { if (g) k_transport<R, true, true><<<grid, block, smem, st>>>(p); else k_transport<R, true, false><<<grid, block, smem, st>>>(p); }
+    else { if (g) k_transport<R, false, true><<<grid, block, smem, st>>>(p); else k_transport<R, false, false><<<grid, block, smem, st>>>(p); }
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+cudaError_t occupancy_of(const void* fn, int block, size_t smem, int* ctas) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+}
+
+}  // namespace
+
+// This file is compiled twice, once per transport precision (TP_BUILD_F32 /
+// TP_BUILD_F64), so that the two halves of the kernels build in parallel.
+#if defined(TP_BUILD_F32)
+cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
                                  cudaStream_t st) {
-  if (grad) k_transport<double, true><<<grid, block, smem, st>>>(p);
-  else k_transport<double, false><<<grid, block, smem, st>>>(p);
-  return cudaGetLastError();
+  return launch_any(p, false, grad, grid, block, smem, st);
 }
 
 cudaError_t launch_transport_ev_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
                                     cudaStream_t st) {
-  if (grad) k_transport_ev<float, true><<<grid, block, smem, st>>>(p);
-  else k_transport_ev<float, false><<<grid, block, smem, st>>>(p);
-  return cudaGetLastError();
+  return launch_any(p, true, grad, grid, block, smem, st);
 }
 
-cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
-                                    cudaStream_t st) {
-  if (grad) k_transport_ev<double, true><<<grid, block, smem, st>>>(p);
-  else k_transport_ev<double, false><<<grid, block, smem, st>>>(p);
-  return cudaGetLastError();
+cudaError_t occupancy_f32(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_of(transport_fn<float>(ev, grad, use_grid), block, smem, ctas);
 }
 
 size_t event_bank_bytes(int precision, bool grad, int block) {
@@ -1400,26 +1442,14 @@ size_t event_bank_bytes(int precision, bool grad, int block) {
   return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
 }
 
-cudaError_t occupancy_transport_ev(int precision, bool grad, int block, size_t smem, int* ctas) {
-  const void* fn;
-  if (precision == TP_FP64) fn = grad ? (const void*)k_transport_ev<double, true> : (const void*)k_transport_ev<double, false>;
-  else fn = grad ? (const void*)k_transport_ev<float, true> : (const void*)k_transport_ev<float, false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+cudaError_t occupancy_transport_ev(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return precision == TP_FP64 ? occupancy_f64(true, grad, use_grid, block, smem, ctas)
+                              : occupancy_f32(true, grad, use_grid, block, smem, ctas);
 }
 
-static cudaError_t set_smem(const void* fn, size_t smem) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-cudaError_t occupancy_transport(int precision, bool grad, int block, size_t smem, int* ctas) {
-  const void* fn;
-  if (precision == TP_FP64) fn = grad ? (const void*)k_transport<double, true> : (const void*)k_transport<double, false>;
-  else fn = grad ? (const void*)k_transport<float, true> : (const void*)k_transport<float, false>;
-  cudaError_t e = set_smem(fn, smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+cudaError_t occupancy_transport(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return precision == TP_FP64 ? occupancy_f64(false, grad, use_grid, block, smem, ctas)
+                              : occupancy_f32(false, grad, use_grid, block, smem, ctas);
 }
 
 cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
@@ -1437,5 +1467,22 @@ cudaError_t launch_backward(const double* J, const double* grad_tallies, const d
                                                  grad_params);
   return cudaGetLastError();
 }
+#endif
+
+#if defined(TP_BUILD_F64)
+cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  return launch_any(p, false, grad, grid, block, smem, st);
+}
+
+cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+                                    cudaStream_t st) {
+  return launch_any(p, true, grad, grid, block, smem, st);
+}
+
+cudaError_t occupancy_f64(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_of(transport_fn<double>(ev, grad, use_grid), block, smem, ctas);
+}
+#endif
 
 }  // namespace tp

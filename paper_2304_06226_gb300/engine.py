@@ -120,7 +120,7 @@ class Scene:
 
     def run(self, n=None, seed: int | None = None, first=None, want_grad: bool = False, stream=None,
             block_size: int = 0, ctas_per_sm: int = 0, records: torch.Tensor | None = None,
-            kernel: int = 0) -> None:
+            kernel: int = 0, graph: bool = False) -> None:
         """Queue histories on `stream` (default: torch's current stream).  n: per
         instance counts (int for one instance, array for many; default: the
         workload's counts)."""
@@ -136,7 +136,7 @@ class Scene:
                      int(want_grad), _stream_handle(stream), block_size, ctas_per_sm,
                      None if records is None else records.data_ptr(),
                      0 if records is None else records.numel() * records.element_size() // C.sizeof(N.tp_record),
-                     kernel)
+                     kernel, int(graph))
         N.tp_run_histories(self.handle, r)
 
     def tally(self, t: int, instance: int = 0, device: bool = True):
@@ -235,9 +235,11 @@ class TransportFn(torch.autograd.Function):
         scene.reset()
         scene.run(n=n, seed=seed, want_grad=True)
         ctx.scene = scene
+        ctx.param_device = params.device
+        ctx.param_dtype = params.dtype
         return scene.means()
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
         g = ctx.scene.backward(grad_out)
-        return g.to(grad_out.device), None, None, None
+        return g.to(device=ctx.param_device, dtype=ctx.param_dtype), None, None, None

@@ -83,7 +83,7 @@ def run_noalloc(N, desc, n, seed):
     out_sq = torch.zeros(tb, dtype=torch.float64, device="cuda")
     counts = np.array([n], dtype=np.uint64)
     run = N.tp_run(seed, counts.ctypes.data_as(C.POINTER(C.c_uint64)), None, 0,
-                   torch.cuda.current_stream().cuda_stream, 0, 0, None, 0, 0)
+                   torch.cuda.current_stream().cuda_stream, 0, 0, None, 0, 0, 0)
     cnt = (C.c_int64 * 8)()
     st = N.lib.tp_run_histories_noalloc(C.byref(d), mats, nm, bias.ctypes.data_as(N.DP) if bias.size else None,
                                         C.byref(run), out_sum.data_ptr(), out_sq.data_ptr(), cnt)
@@ -122,7 +122,7 @@ def test_noalloc_rejects_sizes_beyond_its_limits(env):
     d, mats, nm, bias, keep = marshal(N, desc)
     d.n_instances = 65   # TP_NOALLOC_MAX_INSTANCES + 1
     counts = np.ones(d.n_instances, dtype=np.uint64)
-    run = N.tp_run(1, counts.ctypes.data_as(C.POINTER(C.c_uint64)), None, 0, None, 0, 0, None, 0, 0)
+    run = N.tp_run(1, counts.ctypes.data_as(C.POINTER(C.c_uint64)), None, 0, None, 0, 0, None, 0, 0, 0)
     buf = torch.zeros(8, dtype=torch.float64, device="cuda")
     st = N.lib.tp_run_histories_noalloc(C.byref(d), mats, nm, None, C.byref(run), buf.data_ptr(), buf.data_ptr(), None)
     assert st == N.TP_ERR_INVALID_ARG
