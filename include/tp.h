@@ -194,8 +194,10 @@ typedef struct {
  * stream: a cudaStream_t (NULL = legacy default stream).
  * kernel: TP_KERNEL_HISTORY (one neutron per thread until it ends),
  *   TP_KERNEL_EVENT (neutrons regrouped by event type every event in a
- *   shared-memory bank), or 0: the autotuner times both (and block sizes) on
- *   the scene's first run with and without gradients and keeps the faster.
+ *   shared-memory bank per block), TP_KERNEL_WARPQ (a pool of neutrons per
+ *   warp; each step runs the event type most of them wait for), or 0: the
+ *   autotuner times the variants (and block sizes) on the scene's first run
+ *   with and without gradients and keeps the fastest.
  * block_size / ctas_per_sm: 0 = autotuned / the most that fit on an SM.
  * use_graph: 1 = run as a CUDA graph [work-description copies, work-counter
  *   reset, persistent kernel] captured on the first call with a given launch
@@ -217,7 +219,7 @@ typedef struct {
   int use_graph;
 } tp_run;
 
-enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2 };
+enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2, TP_KERNEL_WARPQ = 3 };
 
 /* Runs histories and accumulates their scores into the scene's tallies
  * (sum w, sum w^2 per bin per instance, and the gradient tallies).  Returns

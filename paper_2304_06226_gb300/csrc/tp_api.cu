@@ -555,7 +555,7 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
   int b = req_block > 0 ? req_block : (s->block > 0 ? s->block : 256);
   if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 256]", b);
   int occ = 0;
-  TP_CUDA(occupancy_transport(s->precision, grad, s->grid_cells > 0, b, smem_bytes(s), &occ));
+  TP_CUDA(occupancy_transport(TP_KERNEL_HISTORY, s->precision, grad, s->grid_cells > 0, b, smem_bytes(s), &occ));
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "block_size %d does not fit on an SM", b);
   int c = req_ctas > 0 ? std::min(req_ctas, occ) : occ;
   *block = b;
@@ -567,19 +567,19 @@ struct LaunchCfg {
   int kernel, block, ctas;
 };
 
-size_t smem_event(const tp_scene* s, bool grad, int block) {
-  return smem_bytes(s) + align16(event_bank_bytes(s->precision, grad, block));
+size_t smem_variant(const tp_scene* s, int variant, bool grad, int block) {
+  return smem_bytes(s) + align16(bank_bytes(variant, s->precision, grad, block));
 }
 
 // Completes a launch configuration (CTAs per SM from the occupancy).
 tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c) {
-  if (kernel == TP_KERNEL_EVENT) {
+  if (kernel == TP_KERNEL_EVENT || kernel == TP_KERNEL_WARPQ) {
     const int b = req_block > 0 ? req_block : 256;
-    if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d: need a multiple of 32 in [32, 256]", b);
+    if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
     int occ = 0;
-    TP_CUDA(occupancy_transport_ev(s->precision, grad, s->grid_cells > 0, b, smem_event(s, grad, b), &occ));
-    if (occ < 1) return fail(TP_ERR_INVALID_ARG, "event kernel block_size %d does not fit on an SM", b);
-    *c = LaunchCfg{TP_KERNEL_EVENT, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ};
+    TP_CUDA(occupancy_transport(kernel, s->precision, grad, s->grid_cells > 0, b, smem_variant(s, kernel, grad, b), &occ));
+    if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
+    *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ};
     return TP_OK;
   }
   int b = 0, ct = 0;
@@ -610,13 +610,9 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   k.chunk = (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
   cudaError_t e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  if (c.kernel == TP_KERNEL_EVENT) {
-    const size_t sm = smem_event(s, grad, c.block);
-    if constexpr (std::is_same<R, double>::value) return launch_transport_ev_f64(k, grad, grid, c.block, sm, st);
-    else return launch_transport_ev_f32(k, grad, grid, c.block, sm, st);
-  }
-  if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, grad, grid, c.block, smem_bytes(s), st);
-  else return launch_transport_f32(k, grad, grid, c.block, smem_bytes(s), st);
+  const size_t sm = smem_variant(s, c.kernel, grad, c.block);
+  if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, c.kernel, grad, grid, c.block, sm, st);
+  else return launch_transport_f32(k, c.kernel, grad, grid, c.block, sm, st);
 }
 
 cudaError_t launch_cfg(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
@@ -639,7 +635,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   Outputs o{scratch, scratch + nb, grad ? scratch + 2 * nb : nullptr,
             grad ? scratch + (2 + s->n_par) * nb : nullptr, cnt};
   const int cand[][2] = {{TP_KERNEL_EVENT, 256}, {TP_KERNEL_EVENT, 128}, {TP_KERNEL_HISTORY, 128},
-                         {TP_KERNEL_HISTORY, 256}};
+                         {TP_KERNEL_HISTORY, 256}, {TP_KERNEL_WARPQ, 256}, {TP_KERNEL_WARPQ, 128}};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -945,7 +941,7 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   if (!s || !r || !r->n_histories) return fail(TP_ERR_INVALID_ARG, "null argument");
   if (!s->have_materials) return fail(TP_ERR_STATE, "tp_set_materials first");
   if (r->want_grad && s->n_par == 0) return fail(TP_ERR_INVALID_ARG, "want_grad without parameters");
-  if (r->kernel < TP_KERNEL_AUTO || r->kernel > TP_KERNEL_EVENT) return fail(TP_ERR_INVALID_ARG, "kernel %d", r->kernel);
+  if (r->kernel < TP_KERNEL_AUTO || r->kernel > TP_KERNEL_WARPQ) return fail(TP_ERR_INVALID_ARG, "kernel %d", r->kernel);
   const bool grad = r->want_grad != 0;
   cudaStream_t st = (cudaStream_t)r->stream;
   if (s->blob_dirty) {
@@ -1300,13 +1296,13 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
       fill_common(&s, k);
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
-      ce = launch_transport_f64(k, false, grid, block, smem_bytes(&s), strm);
+      ce = launch_transport_f64(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
     } else {
       KParams<float> k{};
       fill_common(&s, k);
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
-      ce = launch_transport_f32(k, false, grid, block, smem_bytes(&s), strm);
+      ce = launch_transport_f32(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
     }
     if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
   }

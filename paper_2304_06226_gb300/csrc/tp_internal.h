@@ -108,21 +108,17 @@ struct KParams {
   int* status;
 };
 
-// Launchers (tp_transport.cu).
-cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block,
+// Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ.
+cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
-cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block,
+cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
-cudaError_t occupancy_transport(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas);
-// Event-based variant: shared memory = tables + event_bank_bytes(...).
-cudaError_t launch_transport_ev_f32(const KParams<float>& p, bool grad, int grid, int block,
-                                    size_t smem, cudaStream_t st);
-cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block,
-                                    size_t smem, cudaStream_t st);
-size_t event_bank_bytes(int precision, bool grad, int block);
-cudaError_t occupancy_f32(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas);
-cudaError_t occupancy_f64(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas);
-cudaError_t occupancy_transport_ev(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas);
+// Shared memory of the neutron bank of a variant (added to the staged tables).
+size_t bank_bytes(int variant, int precision, bool grad, int block);
+cudaError_t occupancy_transport(int variant, int precision, bool grad, bool use_grid, int block, size_t smem,
+                                int* ctas);
+cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas);
+cudaError_t occupancy_f64(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas);
 cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
                          double* err, cudaStream_t st);
 cudaError_t launch_backward(const double* J, const double* grad_tallies, const double* scale,

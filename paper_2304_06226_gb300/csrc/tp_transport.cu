@@ -1350,6 +1350,214 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-pool kernel: each warp owns kPool neutrons in shared memory and, every
+// step, runs the event type most of them wait for (new history, advance in a
+// primitive, advance in the world, exit crossing, entry crossing, collision) on
+// up to 32 of them, so the warp executes one code path with most lanes busy.
+// Warps never wait for one another: no CTA barrier after the table copy.
+// ---------------------------------------------------------------------------
+constexpr int kPool = 64;                 // neutrons per warp
+constexpr int kPoolGroups = kPool / 32;   // pool slots per lane
+
+template <typename R, bool GRAD, bool GRID>
+__global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__ KParams<R> kp) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bar;
+  const uint8_t* base = kp.blob;
+  uint32_t tab = 0;
+  if (kp.stage_blob) {
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
+      if (threadIdx.x == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+      return;
+    }
+    base = smem;
+    tab = (kp.blob_bytes + 15u) & ~15u;
+  }
+  View<R> V;
+  V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
+  V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
+  V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
+  V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
+  V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
+  V.nb = reinterpret_cast<const int*>(base + kp.off_nb);
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  Particle<R>* pool = reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)warp * kPool;
+  Particle<R>* park = reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)nwarps * kPool + (size_t)warp * kPool;
+  int* pend = reinterpret_cast<int*>(reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)nwarps * kPool * (GRAD ? 2 : 1)) +
+              warp * 2 * kPool;
+  int* parked = pend + kPool;
+
+  unsigned long long cnt[kNumCounters];
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+#pragma unroll
+  for (int g = 0; g < kPoolGroups; ++g) { pend[g * 32 + lane] = EV_EMPTY; parked[g * 32 + lane] = 0; }
+  __syncwarp();
+  unsigned long long chunk_next = 0, chunk_end = 0;   // warp-uniform
+  bool work_left = true;                              // warp-uniform
+
+  for (;;) {
+    // ---- count what the pool waits for ----
+    unsigned m[6][kPoolGroups];
+#pragma unroll
+    for (int g = 0; g < kPoolGroups; ++g) {
+      const int slot = g * 32 + lane;
+      const int ty = pend[slot] & 15;
+      const bool adv = ty == EV_ADV;
+      const bool inprim = adv && pool[slot].vol >= 0;
+      m[Q_EMPTY][g] = __ballot_sync(kFull, ty == EV_EMPTY);
+      m[Q_ADVP][g] = __ballot_sync(kFull, adv && inprim);
+      m[Q_ADVW][g] = __ballot_sync(kFull, adv && !inprim);
+      m[Q_XEXIT][g] = __ballot_sync(kFull, ty == EV_XEXIT);
+      m[Q_XENT][g] = __ballot_sync(kFull, ty == EV_XENT);
+      m[Q_COLL][g] = __ballot_sync(kFull, ty == EV_COLL);
+    }
+    int count[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      count[q] = 0;
+#pragma unroll
+      for (int g = 0; g < kPoolGroups; ++g) count[q] += __popc(m[q][g]);
+    }
+    // ---- pick the queue: refill when half the pool is free, else the fullest ----
+    int q = -1;
+    if (work_left && count[Q_EMPTY] >= 32) {
+      q = Q_EMPTY;
+    } else {
+      int best = 0;
+#pragma unroll
+      for (int k = 1; k < 6; ++k)
+        if (count[k] > best) { best = count[k]; q = k; }
+      if (q < 0) {
+        if (work_left && count[Q_EMPTY] > 0) q = Q_EMPTY;
+        else break;   // nothing live and no work left
+      }
+    }
+    // ---- lane j takes the j-th slot of queue q ----
+    const int n = min(count[q], 32);
+    int slot = -1;
+    if (lane < n) {
+      int j = lane;
+#pragma unroll
+      for (int g = 0; g < kPoolGroups; ++g) {
+        const int c = __popc(m[q][g]);
+        if (slot < 0) {
+          if (j < c) slot = g * 32 + (int)__fns(m[q][g], 0, j + 1);
+          else j -= c;
+        }
+      }
+    }
+    if (q == Q_EMPTY) {
+      // new histories from the warp's chunk of global indices
+      int taken = 0;
+      while (taken < n) {
+        if (chunk_next >= chunk_end) {
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+          b = __shfl_sync(kFull, b, 0);
+          if (b >= kp.total) { work_left = false; break; }
+          chunk_next = b;
+          chunk_end = min(b + (unsigned long long)kp.chunk, kp.total);
+        }
+        const int avail = (int)min((unsigned long long)(n - taken), chunk_end - chunk_next);
+        if (lane >= taken && lane < taken + avail) {
+          const unsigned long long g = chunk_next + (lane - taken);
+          Particle<R> P;
+          int lo = 0, hi = kp.n_inst - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+          }
+          P.inst = (uint32_t)lo;
+          P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
+          R ip[kMaxPar], dR;
+          load_params(kp, P.inst, ip, &dR);
+          cnt[C_HIST]++;
+          int end = -1;
+          if (source(kp, V, P, dR, &end)) {
+            pool[slot] = P;
+            pend[slot] = EV_ADV;
+          } else {
+            if (end == END_LOST) cnt[C_LOST]++;
+            finish(kp, P, end);
+          }
+        }
+        chunk_next += avail;
+        taken += avail;
+      }
+    } else if (q == Q_ADVP || q == Q_ADVW) {
+      if (slot >= 0) {
+        Particle<R> P = pool[slot];
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        Adv<R> a;
+        const int out = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
+        if (out == kOutCross) {
+          pend[slot] = pend_of<R>(P.vol >= 0 ? EV_XEXIT : EV_XENT, a.face, a.target);
+        } else if (out == kOutColl) {
+          pend[slot] = EV_COLL;
+        } else {
+          finish(kp, P, out);
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        }
+        pool[slot] = P;
+      }
+    } else if (q == Q_XEXIT || q == Q_XENT) {
+      if (slot >= 0) {
+        Particle<R> P = pool[slot];
+        const int pe = pend[slot];
+        const int face = ((pe >> 4) & 15) - 1, target = (pe >> 8) - 4;
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        Particle<R> S;
+        bool spawn = false;
+        const int end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, face, target, &S, &spawn);
+        if (end >= 0) finish(kp, P, end);
+        if (GRAD && spawn) {
+          if (end < 0) { park[slot] = P; parked[slot] = 1; }
+          P = S;
+          pend[slot] = EV_ADV;
+        } else if (end >= 0) {
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        } else {
+          pend[slot] = EV_ADV;
+        }
+        pool[slot] = P;
+      }
+    } else {
+      if (slot >= 0) {
+        Particle<R> P = pool[slot];
+        R ip[kMaxPar], dR;
+        load_params(kp, P.inst, ip, &dR);
+        const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
+        if (end >= 0) {
+          finish(kp, P, end);
+          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+          else pend[slot] = EV_EMPTY;
+        } else {
+          pend[slot] = EV_ADV;
+        }
+        pool[slot] = P;
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) {
+    unsigned long long v = cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0 && v) atomicAdd(kp.counters + i, v);
+  }
+}
+
 // mean and standard error per bin
 __global__ void k_stats(const double* __restrict__ sum, const double* __restrict__ sumsq, double n,
                         int nbins, double* __restrict__ mean, double* __restrict__ err) {
@@ -1390,8 +1598,12 @@ __global__ void k_backward(const double* __restrict__ J, const double* __restric
 
 // kernel pointer for (precision, variant, gradients, grid)
 template <typename R>
-const void* transport_fn(bool ev, bool grad, bool grid) {
-  if (ev) {
+const void* transport_fn(int variant, bool grad, bool grid) {
+  if (variant == TP_KERNEL_WARPQ) {
+    if (grad) return grid ? (const void*)k_transport_wq<R, true, true> : (const void*)k_transport_wq<R, true, false>;
+    return grid ? (const void*)k_transport_wq<R, false, true> : (const void*)k_transport_wq<R, false, false>;
+  }
+  if (variant == TP_KERNEL_EVENT) {
     if (grad) return grid ? (const void*)k_transport_ev<R, true, true> : (const void*)k_transport_ev<R, true, false>;
     return grid ? (const void*)k_transport_ev<R, false, true> : (const void*)k_transport_ev<R, false, false>;
   }
@@ -1400,9 +1612,12 @@ const void* transport_fn(bool ev, bool grad, bool grid) {
 }
 
 template <typename R>
-cudaError_t launch_any(const KParams<R>& p, bool ev, bool grad, int grid, int block, size_t smem, cudaStream_t st) {
+cudaError_t launch_any(const KParams<R>& p, int variant, bool grad, int grid, int block, size_t smem, cudaStream_t st) {
   const bool g = p.use_grid != 0;
-  if (ev) {
+  if (variant == TP_KERNEL_WARPQ) {
+    if (grad) { if (g) k_transport_wq<R, true, true><<<grid, block, smem, st>>>(p); else k_transport_wq<R, true, false><<<grid, block, smem, st>>>(p); }
+    else { if (g) k_transport_wq<R, false, true><<<grid, block, smem, st>>>(p); else k_transport_wq<R, false, false><<<grid, block, smem, st>>>(p); }
+  } else if (variant == TP_KERNEL_EVENT) {
     if (grad) { if (g) k_transport_ev<R, true, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, true, false><<<grid, block, smem, st>>>(p); }
     else { if (g) k_transport_ev<R, false, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, false, false><<<grid, block, smem, st>>>(p); }
   } else {
@@ -1423,33 +1638,30 @@ cudaError_t occupancy_of(const void* fn, int block, size_t smem, int* ctas) {
 // This file is compiled twice, once per transport precision (TP_BUILD_F32 /
 // TP_BUILD_F64), so that the two halves of the kernels build in parallel.
 #if defined(TP_BUILD_F32)
-cudaError_t launch_transport_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
+cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block, size_t smem,
                                  cudaStream_t st) {
-  return launch_any(p, false, grad, grid, block, smem, st);
+  return launch_any(p, variant, grad, grid, block, smem, st);
 }
 
-cudaError_t launch_transport_ev_f32(const KParams<float>& p, bool grad, int grid, int block, size_t smem,
-                                    cudaStream_t st) {
-  return launch_any(p, true, grad, grid, block, smem, st);
+cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_of(transport_fn<float>(variant, grad, use_grid), block, smem, ctas);
 }
 
-cudaError_t occupancy_f32(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return occupancy_of(transport_fn<float>(ev, grad, use_grid), block, smem, ctas);
-}
-
-size_t event_bank_bytes(int precision, bool grad, int block) {
+size_t bank_bytes(int variant, int precision, bool grad, int block) {
   const size_t ps = precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
-  return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
+  if (variant == TP_KERNEL_EVENT)
+    return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
+  if (variant == TP_KERNEL_WARPQ) {
+    const size_t slots = (size_t)(block / 32) * kPool;
+    return ps * slots * (grad ? 2 : 1) + 2 * sizeof(int) * slots;
+  }
+  return 0;
 }
 
-cudaError_t occupancy_transport_ev(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return precision == TP_FP64 ? occupancy_f64(true, grad, use_grid, block, smem, ctas)
-                              : occupancy_f32(true, grad, use_grid, block, smem, ctas);
-}
-
-cudaError_t occupancy_transport(int precision, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return precision == TP_FP64 ? occupancy_f64(false, grad, use_grid, block, smem, ctas)
-                              : occupancy_f32(false, grad, use_grid, block, smem, ctas);
+cudaError_t occupancy_transport(int variant, int precision, bool grad, bool use_grid, int block, size_t smem,
+                                int* ctas) {
+  return precision == TP_FP64 ? occupancy_f64(variant, grad, use_grid, block, smem, ctas)
+                              : occupancy_f32(variant, grad, use_grid, block, smem, ctas);
 }
 
 cudaError_t launch_stats(const double* sum, const double* sumsq, double n, int nbins, double* mean,
@@ -1470,18 +1682,13 @@ cudaError_t launch_backward(const double* J, const double* grad_tallies, const d
 #endif
 
 #if defined(TP_BUILD_F64)
-cudaError_t launch_transport_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
+cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block, size_t smem,
                                  cudaStream_t st) {
-  return launch_any(p, false, grad, grid, block, smem, st);
+  return launch_any(p, variant, grad, grid, block, smem, st);
 }
 
-cudaError_t launch_transport_ev_f64(const KParams<double>& p, bool grad, int grid, int block, size_t smem,
-                                    cudaStream_t st) {
-  return launch_any(p, true, grad, grid, block, smem, st);
-}
-
-cudaError_t occupancy_f64(bool ev, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return occupancy_of(transport_fn<double>(ev, grad, use_grid), block, smem, ctas);
+cudaError_t occupancy_f64(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_of(transport_fn<double>(variant, grad, use_grid), block, smem, ctas);
 }
 #endif
 

@@ -21,7 +21,7 @@ TP_PTS_ENTRY, TP_PTS_EXIT = 0, 1
 TP_PAR_RADIUS, TP_PAR_SCALE, TP_PAR_DENSITY = 0, 1, 2
 TP_SRC_PENCIL, TP_SRC_RECT = 0, 1
 TP_FP32, TP_FP64 = 0, 1
-TP_KERNEL_AUTO, TP_KERNEL_HISTORY, TP_KERNEL_EVENT = 0, 1, 2
+TP_KERNEL_AUTO, TP_KERNEL_HISTORY, TP_KERNEL_EVENT, TP_KERNEL_WARPQ = 0, 1, 2, 3
 TP_MAX_PARAMS = 4
 TP_MAX_TALLIES = 16
 COUNTER_NAMES = ["histories", "events", "collisions", "crossings", "truncated", "lost", "mirror_hits",

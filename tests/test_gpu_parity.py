@@ -48,7 +48,7 @@ def gpu_run(eng, desc, n, records=0, want_grad=False, seed=None, **kw):
 
 def sc_kernel_ok(gpu):
     k, b, c = gpu["scene"].launch()
-    return k in (1, 2) and b > 0 and c > 0
+    return k in (1, 2, 3) and b > 0 and c > 0
 
 
 def assert_totals(m1, e1, m2, e2, rel=1e-3, nsig=4.0):
@@ -60,7 +60,7 @@ def assert_totals(m1, e1, m2, e2, rel=1e-3, nsig=4.0):
 # ---------------------------------------------------------------------------
 # Workload 1 (slab, FP64): history by history
 # ---------------------------------------------------------------------------
-KERNELS = [1, 2]   # TP_KERNEL_HISTORY, TP_KERNEL_EVENT
+KERNELS = [1, 2, 3]   # TP_KERNEL_HISTORY, TP_KERNEL_EVENT, TP_KERNEL_WARPQ
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -116,7 +116,8 @@ def test_slab_first_history_offset_and_split_runs_add_up(eng):
 
 
 @pytest.mark.parametrize("kernel,block,ctas", [(1, 32, 1), (1, 128, 0), (1, 64, 0), (1, 256, 1),
-                                               (2, 32, 1), (2, 128, 0), (2, 256, 0), (2, 256, 1)])
+                                               (2, 32, 1), (2, 128, 0), (2, 256, 0), (2, 256, 1),
+                                               (3, 32, 1), (3, 128, 0), (3, 256, 0), (3, 64, 2)])
 def test_launch_shape_does_not_change_results(eng, kernel, block, ctas):
     n = 30_011   # ragged against every chunk size
     desc = W.slab(g=3.0, n_histories=n, precision="f64")
