@@ -100,7 +100,7 @@ struct tp_scene {
   bool stage_pending = false;
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
-  int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0};
+  int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1};
   // CUDA graph of the last graph run and the launch it was captured for
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -565,27 +565,29 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
 
 struct LaunchCfg {
   int kernel, block, ctas;
+  int stage;   // copy the scene tables into shared memory
 };
 
-size_t smem_variant(const tp_scene* s, int variant, bool grad, int block) {
-  return smem_bytes(s) + align16(bank_bytes(variant, s->precision, grad, block));
+size_t smem_variant(const tp_scene* s, int variant, bool grad, int block, int stage) {
+  return (stage ? align16(s->blob_bytes) : 0) + align16(bank_bytes(variant, s->precision, grad, block));
 }
 
+// Tables larger than this are offered to the autotuner unstaged as well
+// (read through L1/L2), which leaves room for more blocks per SM.
+constexpr uint32_t kStageChoiceBytes = 16 * 1024;
+
 // Completes a launch configuration (CTAs per SM from the occupancy).
-tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c) {
-  if (kernel == TP_KERNEL_EVENT || kernel == TP_KERNEL_WARPQ) {
-    const int b = req_block > 0 ? req_block : 256;
-    if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
-    int occ = 0;
-    TP_CUDA(occupancy_transport(kernel, s->precision, grad, s->grid_cells > 0, b, smem_variant(s, kernel, grad, b), &occ));
-    if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
-    *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ};
-    return TP_OK;
-  }
-  int b = 0, ct = 0;
-  tp_status st = pick_launch(s, grad, req_block, req_ctas, &b, &ct);
-  if (st != TP_OK) return st;
-  *c = LaunchCfg{TP_KERNEL_HISTORY, b, ct};
+// stage: -1 = stage the tables when they fit (<= kMaxStagedBlob).
+tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c, int stage = -1) {
+  if (stage < 0) stage = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
+  if (stage && s->blob_bytes > kMaxStagedBlob) return fail(TP_ERR_INVALID_ARG, "tables too large to stage");
+  const int b = req_block > 0 ? req_block : 256;
+  if (b % 32 != 0 || b < 32 || b > 256)
+    return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
+  int occ = 0;
+  TP_CUDA(occupancy_transport(kernel, s->precision, grad, s->grid_cells > 0, b, smem_variant(s, kernel, grad, b, stage), &occ));
+  if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
+  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage};
   return TP_OK;
 }
 
@@ -605,12 +607,13 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   k.records = records;
   k.n_records = records ? n_records : 0;
   k.sum = o.sum; k.sumsq = o.sumsq; k.J = o.J; k.J2 = o.J2; k.counters = o.counters;
+  k.stage_blob = c.stage;
   const int grid = s->sm_count * c.ctas;
   const long long warps = (long long)grid * (c.block / 32);
   k.chunk = (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
   cudaError_t e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  const size_t sm = smem_variant(s, c.kernel, grad, c.block);
+  const size_t sm = smem_variant(s, c.kernel, grad, c.block, c.stage);
   if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, c.kernel, grad, grid, c.block, sm, st);
   else return launch_transport_f32(k, c.kernel, grad, grid, c.block, sm, st);
 }
@@ -642,9 +645,12 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   float best = 1e30f;
   LaunchCfg pick{0, 0, 0};
   tp_status result = TP_OK;
-  for (const auto& c : cand) {
+  const int nstage = s->blob_bytes > kStageChoiceBytes && s->blob_bytes <= kMaxStagedBlob ? 2 : 1;
+  for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]) * nstage; ++ci) {
+    const int* c = cand[ci / nstage];
+    const int stage = nstage == 2 ? (ci % 2 == 0 ? 1 : 0) : -1;
     LaunchCfg cfg;
-    if (resolve(s, grad, c[0], c[1], 0, &cfg) != TP_OK) continue;   // does not fit: skip
+    if (resolve(s, grad, c[0], c[1], 0, &cfg, stage) != TP_OK) continue;   // does not fit: skip
     for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
       cudaEventRecord(a, st);
       ce = launch_cfg(s, cfg, grad, seed, trial, nullptr, 0, o, st);
@@ -665,6 +671,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   if (pick.kernel == 0) return fail(TP_ERR_INVALID_ARG, "no launch configuration fits");
   s->tuned_kernel[grad] = pick.kernel;
   s->tuned_block[grad] = pick.block;
+  s->tuned_stage[grad] = pick.stage;
   return TP_OK;
 }
 
@@ -675,7 +682,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
 tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* r, unsigned long long total,
                     const Outputs& o, cudaStream_t st) {
   const unsigned long long key[8] = {(unsigned long long)cfg.kernel, (unsigned long long)cfg.block,
-                                     (unsigned long long)cfg.ctas, (unsigned long long)grad, r->seed, total,
+                                     (unsigned long long)(cfg.ctas * 2 + cfg.stage), (unsigned long long)grad, r->seed, total,
                                      (unsigned long long)(uintptr_t)r->records, r->records ? r->n_records : 0};
   if (!s->graph || std::memcmp(key, s->graph_key, sizeof key) != 0) {
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
@@ -977,7 +984,8 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
     if (block == 0) block = s->tuned_block[grad];
   }
   LaunchCfg cfg;
-  tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg);
+  tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg,
+                        r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : -1);
   if (e != TP_OK) return e;
   Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
   if (r->use_graph) {

@@ -1357,7 +1357,11 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
 // up to 32 of them, so the warp executes one code path with most lanes busy.
 // Warps never wait for one another: no CTA barrier after the table copy.
 // ---------------------------------------------------------------------------
-constexpr int kPool = 64;                 // neutrons per warp
+#ifndef TP_POOL
+#define TP_POOL 64
+#endif
+constexpr int kPool = TP_POOL;            // neutrons per warp (a multiple of 32)
+static_assert(kPool % 32 == 0, "pool size");
 constexpr int kPoolGroups = kPool / 32;   // pool slots per lane
 
 template <typename R, bool GRAD, bool GRID>
