@@ -482,11 +482,11 @@ __device__ __forceinline__ int bin1(R x, R lo, R hi, R inv_w, int n) {
 }
 
 template <typename R>
-__device__ __forceinline__ int tally_bin(const DTally<R>& T, const Particle<R>& P) {
+__device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam) {
   switch (T.kind) {
     case TP_TALLY_COUNT: return 0;
     case TP_TALLY_ANGULAR: {
-      const R v0 = P.x[0] - T.origin[0], v1 = P.x[1] - T.origin[1], v2 = P.x[2] - T.origin[2];
+      const R v0 = x0 - T.origin[0], v1 = x1 - T.origin[1], v2 = x2 - T.origin[2];
       const R dt = v0 * T.axis[0] + v1 * T.axis[1] + v2 * T.axis[2];
       const R c0 = v1 * T.axis[2] - v2 * T.axis[1], c1 = v2 * T.axis[0] - v0 * T.axis[2],
               c2 = v0 * T.axis[1] - v1 * T.axis[0];
@@ -494,36 +494,42 @@ __device__ __forceinline__ int tally_bin(const DTally<R>& T, const Particle<R>& 
       return bin1(th, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
     }
     case TP_TALLY_PSD: {
-      const int bx = bin1(P.x[0], T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-      const int by = bin1(P.x[1], T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+      const int bx = bin1(x0, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      const int by = bin1(x1, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
       return (bx < 0 || by < 0) ? -1 : bx * T.nb1 + by;
     }
     default: {
-      const int bl = bin1(P.lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-      const int bx = bin1(P.x[0], T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+      const int bl = bin1(lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      const int bx = bin1(x0, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
       return (bl < 0 || bx < 0) ? -1 : bl * T.nb1 + bx;
     }
   }
 }
 
+// Scoring at a particle tracing state: every tally of `mask` (filtered by face
+// and scattering number) gets w and w^2 in its bin, and the gradient tallies
+// w A_p (a derivative secondary scores w into the radius tally only).
 template <typename R, bool GRAD>
-__device__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>& P, unsigned mask, int face) {
+__device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>* tallies, unsigned mask, int face,
+                                       R x0, R x1, R x2, R lam, R w_, R A0, R A1, R A2, R A3, int nscat,
+                                       uint32_t inst, int secondary) {
+  const R A[kMaxPar] = {A0, A1, A2, A3};
   while (mask) {
     const int t = __ffs(mask) - 1;
     mask &= mask - 1;
-    const DTally<R>& T = V.tallies[t];
+    const DTally<R>& T = tallies[t];
     if (T.face >= 0 && T.face != face) continue;
-    if (T.scat >= 0 && T.scat != P.nscat) continue;
-    const int b = tally_bin(T, P);
+    if (T.scat >= 0 && T.scat != nscat) continue;
+    const int b = tally_bin(T, x0, x1, x2, lam);
     if (b < 0) continue;
-    const unsigned long long idx = (unsigned long long)P.inst * kp.total_bins + T.offset + b;
-    const double w = (double)P.w;
+    const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
+    const double w = (double)w_;
     const unsigned long long stride = (unsigned long long)kp.n_inst * kp.total_bins;
-    if (!P.secondary) {
+    if (!secondary) {
       agg_add2(kp.sum, kp.sumsq, idx, w, w * w);
       if (GRAD) {
         for (int p = 0; p < kp.npar; ++p) {
-          const double g = w * (double)P.A[p];
+          const double g = w * (double)A[p];
           agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
         }
       }
@@ -531,6 +537,13 @@ __device__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>&
       agg_add2(kp.J, kp.J2, kp.radius_par * stride + idx, w, w * w);
     }
   }
+}
+
+template <typename R, bool GRAD>
+__device__ __forceinline__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>& P, unsigned mask,
+                                      int face) {
+  score_out<R, GRAD>(kp, V.tallies, mask, face, P.x[0], P.x[1], P.x[2], P.lam, P.w, P.A[0], P.A[1], P.A[2],
+                     P.A[3], P.nscat, P.inst, P.secondary);
 }
 
 // ---------------------------------------------------------------------------
