@@ -30,10 +30,15 @@ sys.path.insert(0, str(ROOT))
 METRIC = "histories/s on 1 GB300: plain vs batched+adjoint, at matched tally error"
 UNIT = "histories/s"
 POWDER_N = 100_000_000
-# Thread instructions the history-based transport kernel executes per history
-# (ncu smsp__thread_inst_executed.sum / histories on the 2e6-history case of the
-# workload): the per-unit figure of the ALU-issue roofline.
-INST_PER_HISTORY = {"powder": 4092}
+# Algorithmic work per history: thread instructions the history-based kernel
+# (one neutron per thread, no regrouping overhead) executes per history, from
+# ncu smsp__thread_inst_executed.sum / histories on a small case of each
+# workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
+# the ALU-issue roofline, whichever kernel variant runs.
+INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638}
+# DRAM bytes of one full-size launch of the kernel variant the autotuner picks
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
+TRAFFIC_PER_LAUNCH = {("powder", 3): 324352 + 11930368, ("powder", 1): 634880 + 68608}
 SM_COUNT = 152
 LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -200,8 +205,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
     if rank != 0:
         return None
-    # the per-unit figure was measured on the history-based kernel
-    inst_ph = INST_PER_HISTORY.get(args.workload) if sc.launch()[0] == 1 else None
+    inst_ph = INST_PER_HISTORY.get(args.workload)
+    traffic = TRAFFIC_PER_LAUNCH.get((args.workload, sc.launch()[0])) if not args.histories else None
     clocks = clk.summary()
     peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
     achieved = inst_ph * tot / (sum(kernel_ms) / 1e3) if inst_ph else None
@@ -215,7 +220,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "launch": dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch())),
             "parallelism": f"history ids sharded over {world} GPU(s)"}),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "per_unit": inst_ph, "peak_basis": "152 SMs x 128 lanes x 2070 MHz"},
         "kernel_ms": kernel_ms,
         "tally": {"mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
