@@ -35,7 +35,7 @@ POWDER_N = 100_000_000
 # ncu smsp__thread_inst_executed.sum / histories on a small case of each
 # workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
 # the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638}
+INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638, "batched": 13454}
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
 TRAFFIC_PER_LAUNCH = {("powder", 3): 324352 + 11930368, ("powder", 1): 634880 + 68608}
@@ -54,6 +54,9 @@ def workload_desc(name: str):
         return W.slab(g=3.0, n_histories=1_000_000), "slab, bias 3, 1e6 histories, FP64 transport"
     if name == "imaging":
         return W.imaging(n_histories=1_000_000_000), "CSG imaging 1000 primitives, 512^2 PSD, 1e9 histories, FP32 transport"
+    if name == "batched":
+        return W.batched(), ("256 powder instances, uneven history counts (5.9e8 total), gradients w.r.t. "
+                             "radius, scale, density + backward, FP32 transport")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -133,18 +136,34 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     desc, label = workload_desc(args.workload)
+    grad = args.workload == "batched"
     if args.histories:
-        desc["instances"]["counts"][0] = args.histories
-        label = label.replace("1e8 histories", f"{args.histories:.0e} histories")
-    n = int(desc["instances"]["counts"][0])
+        if grad:   # keep the instance mix, scale the counts to the requested total
+            c = desc["instances"]["counts"].astype(np.float64)
+            desc["instances"]["counts"] = np.maximum(1, np.rint(c * args.histories / c.sum())).astype(np.int64)
+            label += f" (scaled to {int(desc['instances']['counts'].sum()):.2e} histories)"
+        else:
+            desc["instances"]["counts"][0] = args.histories
+            label = label.replace("1e8 histories", f"{args.histories:.0e} histories")
+    n = int(desc["instances"]["counts"].sum())
     sc = Scene(desc)
+    bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
+    runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, graph=True,
+                                   first=first)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     first = rank * n   # disjoint history ids per rank: weak scaling
 
-    # ---- warm-up (also JIT-free: the library is ahead-of-time compiled) ----
+    def step(st=None):
+        if grad:
+            runs(st)
+            sc.backward(bgrad, stream=st)
+        else:
+            sc.run(n, first=first, stream=st, kernel=args.kernel)
+
+    # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
     for _ in range(args.warmup):
-        sc.run(n, first=first, kernel=args.kernel)
+        step()
     torch.cuda.synchronize()
     sc.reset()
     if dist:
@@ -157,7 +176,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         for k in range(args.steps):
             flush_l2(flush)
             ev[k][0].record(stream)
-            sc.run(n, first=first, stream=stream, kernel=args.kernel)
+            step(stream)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -171,8 +190,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     tot = n * args.steps
     value = world * tot / dev_s
     # ---- tally error of the integrated detector total (per history) ----
-    raw = sc.raw(0)
-    N = float(tot)
+    q = int(np.argsort(sc.counts)[len(sc.counts) // 2]) if grad else 0   # median-count instance
+    raw = sc.raw(q)
+    N = float(sc.counts[q] * args.steps) if grad else float(tot)
     mean_tot = raw["sum"].sum() / N
     # rel. standard error of the integrated total: each history hits at most one bin
     var = raw["sumsq"].sum() / N - mean_tot ** 2
@@ -187,20 +207,26 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    host_grad = np.empty((sc.n_inst, max(1, sc.n_par)))
     for k in range(e2e_steps):
         sc.reset()
-        sc.run(n, first=first, kernel=args.kernel)
+        if grad:
+            runs()
+            g = sc.backward(bgrad)
+            host_grad[:, : sc.n_par] = g.cpu().numpy()
+        else:
+            sc.run(n, first=first, kernel=args.kernel)
         for t in range(len(sc.tally_bins)):
             o = sc.tally_off[t]
-            NN.tp_read_tallies(sc.handle, t, 0, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
+            NN.tp_read_tallies(sc.handle, t, q, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
     e2e_s = time.perf_counter() - t0
     e2e_value = world * n * e2e_steps / e2e_s
     h2d = 2 * 8 * sc.n_inst + 8          # history counts, first ids, prefix (per run)
-    d2h = 2 * 8 * sc.total_bins          # means and standard errors
+    d2h = 2 * 8 * sc.total_bins + (8 * sc.n_inst * sc.n_par if grad else 0)   # means, errors, gradients
 
     # ---- batched + adjoint ----
     batched = None
-    if args.batched and rank == 0:
+    if args.batched and rank == 0 and not grad:
         batched = run_batched(args, W, Scene, torch)
 
     if rank != 0:
@@ -277,8 +303,16 @@ def run_batched(args, W, Scene, torch) -> dict:
     m = raw["sum"].sum() / N
     rel = math.sqrt(max(raw["sumsq"].sum() / N - m * m, 0.0) / (N - 1)) / m
     hist_s = total * steps / t
+    launch = dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch()))
+    fw_s = sum(fw_ms) / 1e3
+    achieved = INST_PER_HISTORY["batched"] * total * steps / fw_s
+    peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
     sc.close()
     return {"value": hist_s, "unit": UNIT, "instances": int(len(counts)), "histories_per_step": total,
+            "launch": launch,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
+                         "frac": achieved / peak, "traffic": None, "per_unit": INST_PER_HISTORY["batched"],
+                         "kernel": "transport forward with score-function accumulators"},
             "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
             "rel_stderr_total_median_instance": rel,
             "s_to_eps_per_instance": (rel / 1e-3) ** 2 * N / (hist_s / len(counts))}

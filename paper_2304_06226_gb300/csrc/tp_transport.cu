@@ -111,6 +111,24 @@ struct View {
   const int* nb;
 };
 
+// Register arrays are only indexed with compile-time indices (a runtime index
+// would move them to local memory): these select / update element i.
+template <typename R>
+__device__ __forceinline__ R sel(const R (&v)[kMaxPar], int i, R dflt) {
+  R r = dflt;
+#pragma unroll
+  for (int k = 0; k < kMaxPar; ++k)
+    if (k == i) r = v[k];
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ void add_at(R (&v)[kMaxPar], int i, R x) {
+#pragma unroll
+  for (int k = 0; k < kMaxPar; ++k)
+    if (k == i) v[k] += x;
+}
+
 // ---------------------------------------------------------------------------
 // Cross sections
 // ---------------------------------------------------------------------------
@@ -127,10 +145,10 @@ __device__ __forceinline__ int active_lines(const View<R>& V, const DMat<R>& m, 
 }
 
 template <typename R>
-__device__ __forceinline__ void sigma(const View<R>& V, int mat, const R* ip, R lam, R sig[TP_NPROC]) {
+__device__ __forceinline__ void sigma(const View<R>& V, int mat, const R (&ip)[kMaxPar], R lam, R sig[TP_NPROC]) {
   const DMat<R>& m = V.mats[mat];
-  const R dens = m.density_par >= 0 ? ip[m.density_par] : R(1);
-  const R scale = m.scale_par >= 0 ? ip[m.scale_par] : R(1);
+  const R dens = sel(ip, m.density_par, R(1));
+  const R scale = sel(ip, m.scale_par, R(1));
   sig[TP_PROC_ABS] = dens * (m.abs_1v ? m.sig_abs_ref * lam * R(1.0 / 1.8) : m.sig_abs_ref);
   sig[TP_PROC_INC] = dens * m.sig_inc;
   R sb = R(0);
@@ -528,7 +546,9 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     if (!secondary) {
       agg_add2(kp.sum, kp.sumsq, idx, w, w * w);
       if (GRAD) {
-        for (int p = 0; p < kp.npar; ++p) {
+#pragma unroll
+        for (int p = 0; p < kMaxPar; ++p) {
+          if (p >= kp.npar) break;
           const double g = w * (double)A[p];
           agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
         }
@@ -625,7 +645,7 @@ __device__ __forceinline__ void scatter_dir(const View<R>& V, int mat, int proc,
 // c = +Sigma_j,in, -Sigma_j,out over the scattering processes j.  Returns true
 // if a secondary was created in *S.
 template <typename R>
-__device__ __noinline__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
+__device__ __forceinline__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar],
                                 R dR, int mi, int mo, const R n[3], Particle<R>* S,
                                 unsigned long long* cnt) {
   const R cosn = fabs(P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2]);
@@ -633,7 +653,7 @@ __device__ __noinline__ bool radius_crossing(const KParams<R>& kp, const View<R>
   R si[TP_NPROC] = {R(0), R(0), R(0)}, so[TP_NPROC] = {R(0), R(0), R(0)};
   if (mi >= 0) sigma(V, mi, ip, P.lam, si);
   if (mo >= 0) sigma(V, mo, ip, P.lam, so);
-  P.A[kp.radius_par] -= ((si[0] + si[1] + si[2]) - (so[0] + so[1] + so[2])) / cosn;
+  add_at(P.A, kp.radius_par, -((si[0] + si[1] + si[2]) - (so[0] + so[1] + so[2])) / cosn);
   const R term[4] = {si[TP_PROC_INC], si[TP_PROC_BRAGG], -so[TP_PROC_INC], -so[TP_PROC_BRAGG]};
   const R C = fabs(term[0]) + fabs(term[1]) + fabs(term[2]) + fabs(term[3]);
   if (!(C > R(0))) return false;
@@ -646,12 +666,17 @@ __device__ __noinline__ bool radius_crossing(const KParams<R>& kp, const View<R>
     acc += fabs(term[i]);
     if (pick == 3 && i < 3 && pickv < acc) pick = i;
   }
-  while (term[pick] == R(0) && pick > 0) --pick;
+  // guard against rounding at the top end: the last non-zero term at or below pick
+  R tp = R(0);
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    if (i <= pick && tp == R(0) && term[i] != R(0)) { tp = term[i]; pick = i; }
+  }
   const int mat = pick < 2 ? mi : mo;
   const int proc = (pick & 1) ? TP_PROC_BRAGG : TP_PROC_INC;
   *S = P;
   S->secondary = 1;
-  S->w = P.w * (term[pick] > R(0) ? R(1) : R(-1)) * C / cosn;
+  S->w = P.w * (tp > R(0) ? R(1) : R(-1)) * C / cosn;
   S->nscat = P.nscat + 1;
   S->sub0 = 4u + 2u * P.nsec;
   S->k = 0;
@@ -768,7 +793,7 @@ struct Adv {
 };
 
 template <typename R, bool GRAD, bool GRID>
-__device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+__device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
                        unsigned long long* cnt, Adv<R>& a) {
   const R INF = Tr<R>::inf();
   P.k += 1;
@@ -821,7 +846,9 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   if (sig_g != sig_t) P.w *= d_exp((sig_g - sig_t) * x);
   if (GRAD && mat >= 0 && !P.secondary) {
     const DMat<R>& m = V.mats[mat];
-    for (int p = 0; p < kp.npar; ++p) {
+#pragma unroll
+    for (int p = 0; p < kMaxPar; ++p) {
+      if (p >= kp.npar) break;
       if (kp.param_kind[p] == TP_PAR_DENSITY && m.density_par == p) P.A[p] -= sig_t * x;
       if (kp.param_kind[p] == TP_PAR_SCALE && m.scale_par == p) P.A[p] -= sig[TP_PROC_BRAGG] * x;
     }
@@ -832,7 +859,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
 // Relocation at the boundary reached by advance (face / target of `a`).
 // spawn: set when a radius-derivative secondary was created into *S.
 template <typename R, bool GRAD>
-__device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+__device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
                      unsigned long long* cnt, int face, int target, Particle<R>* S, bool* spawn) {
   cnt[C_CROSS]++;
   if (P.vol >= 0) {
@@ -932,7 +959,9 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
   else j = (m.g[1] * sig[1] > R(0)) ? 1 : 0;
   P.w /= m.g[j];
   if (GRAD && !P.secondary) {
-    for (int p = 0; p < kp.npar; ++p) {
+#pragma unroll
+    for (int p = 0; p < kMaxPar; ++p) {
+      if (p >= kp.npar) break;
       if (kp.param_kind[p] == TP_PAR_DENSITY && m.density_par == p) P.A[p] += R(1);
       if (kp.param_kind[p] == TP_PAR_SCALE && m.scale_par == p && j == TP_PROC_BRAGG) P.A[p] += R(1);
     }
@@ -957,7 +986,7 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
 // Collision after a separate advance: the event's random numbers and cross
 // sections are recomputed from the neutron's state (event k is unchanged).
 template <typename R, bool GRAD>
-__device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip,
+__device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar],
                              unsigned long long* cnt) {
   const uint4 r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
   R sig[TP_NPROC];
@@ -970,7 +999,7 @@ __device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>
 
 // One whole event (history-based kernel).
 template <typename R, bool GRAD, bool GRID>
-__device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R* ip, R dR,
+__device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
                     unsigned long long* cnt, Particle<R>* S, bool* spawn) {
   Adv<R> a;
   const int r = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
@@ -1096,7 +1125,7 @@ __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KP
         P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
 #pragma unroll
         for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)kp.inst_params[(size_t)lo * kMaxPar + i];
-        dR = kp.radius_par >= 0 ? ip[kp.radius_par] - kp.radius_nominal : R(0);
+        dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
         cnt[C_HIST]++;
         int end = -1;
         alive = source(kp, V, P, dR, &end);
@@ -1156,11 +1185,11 @@ __device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pr
 }
 
 template <typename R>
-__device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst, R* ip, R* dR) {
+__device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst, R (&ip)[kMaxPar], R* dR) {
   const double* q = kp.inst_params + (size_t)inst * kMaxPar;
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)__ldg(q + i);
-  *dR = kp.radius_par >= 0 ? ip[kp.radius_par] - kp.radius_nominal : R(0);
+  *dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
 }
 
 template <typename R>

@@ -358,3 +358,17 @@ def test_imaging_1000_primitives_fp32_statistics(eng, orc):
         j1, f1 = stats(gpu["raw"]["J"][p], gpu["raw"]["J2"][p], n)
         j2, f2 = stats(o["J"][p], o["J2"][p], n)
         assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_event_cap_truncates_and_counts_like_the_oracle(eng, orc, kernel):
+    """A per-history event cap bounds every neutron's loop on the device; the
+    truncated histories are counted and score nothing, exactly as in the
+    oracle (FP64, shared streams)."""
+    n = 20_000
+    desc = W.slab(g=3.0, n_histories=n, precision="f64")
+    desc["event_cap"] = 3
+    gpu = gpu_run(eng, desc, n, kernel=kernel)
+    o = orc.OracleScene(desc).run(n)
+    assert gpu["counters"]["truncated"] == o["counters"]["truncated"] > 1000
+    assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
