@@ -336,20 +336,36 @@ def cpu_baseline(args, desc, n_full) -> dict:
 def run_reference(args, rank: int) -> dict | None:
     if rank != 0:
         return None
+    import numpy as np
     from oracle.oracle import OracleScene
     desc, label = workload_desc(args.workload)
     n = int(desc["instances"]["counts"][0])
     cores = os.cpu_count() or 1
     sc = OracleScene(desc)
     per_step = args.ref_sample
+    counts = desc["instances"]["counts"]
+    if args.workload == "batched":
+        # a bounded sample of every instance, in proportion to its count, with gradients
+        share = np.maximum(1, np.rint(per_step * counts / counts.sum())).astype(np.int64)
+        per_step = int(share.sum())
+
+        def one(k, scale=1.0):
+            for q, m in enumerate(share):
+                m = max(1, int(m * scale))
+                sc.run(m, inst=q, first=k * m, threads=cores, want_grad=True)
+    else:
+        def one(k, scale=1.0):
+            m = max(1, int(per_step * scale))
+            sc.run(m, first=k * per_step, threads=cores)
     for k in range(args.warmup):
-        sc.run(min(per_step, 200_000), first=k * per_step, threads=cores)
+        one(k, 0.1)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        sc.run(per_step, first=k * per_step, threads=cores)
+        one(k)
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
-    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
