@@ -39,6 +39,9 @@ INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
 TRAFFIC_PER_LAUNCH = {("powder", 3): 324352 + 11930368, ("powder", 1): 634880 + 68608}
+# The tally whose integrated total defines "matched tally error" per workload
+# (each history scores it at most once).
+FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1}
 SM_COUNT = 152
 LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -54,6 +57,9 @@ def workload_desc(name: str):
         return W.slab(g=3.0, n_histories=1_000_000), "slab, bias 3, 1e6 histories, FP64 transport"
     if name == "imaging":
         return W.imaging(n_histories=1_000_000_000), "CSG imaging 1000 primitives, 512^2 PSD, 1e9 histories, FP32 transport"
+    if name == "total_scattering":
+        return W.total_scattering(n_histories=100_000_000), ("total scattering: pencil on a 1.2 cm fcc-powder sphere, 4 pi "
+                                                             "detector, Q per scattering order, 1e8 histories, FP32 transport")
     if name == "batched":
         return W.batched(), ("256 powder instances, uneven history counts (5.9e8 total), gradients w.r.t. "
                              "radius, scale, density + backward, FP32 transport")
@@ -193,11 +199,13 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     q = int(np.argsort(sc.counts)[len(sc.counts) // 2]) if grad else 0   # median-count instance
     raw = sc.raw(q)
     N = float(sc.counts[q] * args.steps) if grad else float(tot)
-    mean_tot = raw["sum"].sum() / N
+    ft = FIGURE_TALLY.get(args.workload, 0)
+    lo, hi = sc.tally_off[ft], sc.tally_off[ft + 1]
+    mean_tot = raw["sum"][lo:hi].sum() / N
     # rel. standard error of the integrated total: each history hits at most one bin
-    var = raw["sumsq"].sum() / N - mean_tot ** 2
+    var = raw["sumsq"][lo:hi].sum() / N - mean_tot ** 2
     rel_err = math.sqrt(max(var, 0.0) / (N - 1)) / mean_tot
-    fom_plain = 1.0 / (rel_err ** 2 * (dev_s / world))
+    fom_plain = 1.0 / (rel_err ** 2 * (dev_s / world)) if rel_err > 0 else None
 
     # ---- end to end through the public API with host buffers ----
     import ctypes as C
@@ -249,7 +257,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "per_unit": inst_ph, "peak_basis": "152 SMs x 128 lanes x 2070 MHz"},
         "kernel_ms": kernel_ms,
-        "tally": {"mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
+        "tally": {"figure_tally": ft, "mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
                   "counters": counters},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
@@ -371,7 +379,7 @@ def run_reference(args, rank: int) -> dict | None:
             "impl": "reference",
             "config": workload_config(args.workload, label, {"histories_per_step": per_step}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} histories per step of the {n}-history workload"},
+                             "sample": f"{per_step} histories per step of the {int(counts.sum())}-history workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

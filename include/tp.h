@@ -55,9 +55,12 @@ enum { TP_BOX = 0, TP_TUBE = 1, TP_SPHERE = 2 };
 enum { TP_ROLE_BULK = 0, TP_ROLE_DETECTOR = 1, TP_ROLE_BLACK = 2 };
 /* Processes, in the order they are sampled. */
 enum { TP_PROC_ABS = 0, TP_PROC_INC = 1, TP_PROC_BRAGG = 2, TP_NPROC = 3 };
-/* Scorers (§3.4, Table tableScorer): a count, Angular, PSD (x,y), and a
- * wavelength x position monitor (WlSpectrum crossed with a PSD axis). */
-enum { TP_TALLY_COUNT = 0, TP_TALLY_ANGULAR = 1, TP_TALLY_PSD = 2, TP_TALLY_WLX = 3 };
+/* Scorers (§3.4, Table tableScorer): a count, Angular, PSD (x,y), a
+ * wavelength x position monitor (WlSpectrum crossed with a PSD axis),
+ * MultiScat (number of scatterings) and DeltaMomentum (elastic momentum
+ * transfer, Eq. eQelastic). */
+enum { TP_TALLY_COUNT = 0, TP_TALLY_ANGULAR = 1, TP_TALLY_PSD = 2, TP_TALLY_WLX = 3,
+       TP_TALLY_MULTISCAT = 4, TP_TALLY_DQ = 5 };
 /* Particle tracing states that trigger scorers (§3.4). */
 enum { TP_PTS_ENTRY = 0, TP_PTS_EXIT = 1 };
 /* Differentiable instance parameters. */
@@ -93,7 +96,11 @@ typedef struct { double m, R0, Qc, alpha, W; } tp_mirror;
 /* A scorer.  kind TP_TALLY_ANGULAR bins the angle between (position - origin)
  * and axis over [lo[0], hi[0]) in nbins[0] bins; TP_TALLY_PSD bins x over
  * [lo[0],hi[0]) and y over [lo[1],hi[1]); TP_TALLY_WLX bins the wavelength over
- * [lo[0],hi[0]) and x over [lo[1],hi[1]).  Bins are laid out axis-0 major.
+ * [lo[0],hi[0]) and x over [lo[1],hi[1]); TP_TALLY_MULTISCAT bins the number of
+ * scatterings over [lo[0], hi[0]); TP_TALLY_DQ bins Q = 4 pi sin(theta/2)/lambda
+ * (1/A) over [lo[0], hi[0]), theta being the angle between (position - origin)
+ * and axis (origin = sample position, axis = beam direction: the elastic
+ * momentum transfer of Eq. eQelastic).  Bins are laid out axis-0 major.
  * trigger TP_PTS_ENTRY / TP_PTS_EXIT of `volume` (primitive index, -1 = world).
  * face: -1 any, else the face id (box 2*axis + (1 for the + face); tube 0
  *   outer, 1 inner, 2 -cap, 3 +cap; sphere 0 outer, 1 inner).

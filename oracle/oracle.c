@@ -349,18 +349,28 @@ static int bin1(double x, double lo, double hi, int n) {
   return (b >= 0 && b < n) ? b : -1;
 }
 
-/* Bin of tally t for a particle at r with wavelength lambda, or -1. */
-static int tally_bin(const or_tally* T, const double r[3], double lambda) {
+/* Angle between (r - origin) and the tally axis. */
+static double tally_angle(const or_tally* T, const double r[3]) {
+  double v[3] = {r[0] - T->origin[0], r[1] - T->origin[1], r[2] - T->origin[2]};
+  double len = sqrt(dot3(v, v));
+  double al = sqrt(dot3(T->axis, T->axis));
+  double c = dot3(v, T->axis) / (len * al);
+  if (c > 1.0) c = 1.0;
+  if (c < -1.0) c = -1.0;
+  return acos(c);
+}
+
+/* Bin of tally t for a particle at r with wavelength lambda after nscat
+ * scatterings, or -1. */
+static int tally_bin(const or_tally* T, const double r[3], double lambda, int nscat) {
   switch (T->kind) {
     case OR_T_COUNT: return 0;
-    case OR_T_ANGULAR: {
-      double v[3] = {r[0] - T->origin[0], r[1] - T->origin[1], r[2] - T->origin[2]};
-      double len = sqrt(dot3(v, v));
-      double al = sqrt(dot3(T->axis, T->axis));
-      double c = dot3(v, T->axis) / (len * al);
-      if (c > 1.0) c = 1.0;
-      if (c < -1.0) c = -1.0;
-      return bin1(acos(c), T->lo[0], T->hi[0], T->nb[0]);
+    case OR_T_ANGULAR: return bin1(tally_angle(T, r), T->lo[0], T->hi[0], T->nb[0]);
+    case OR_T_MULTISCAT: return bin1((double)nscat, T->lo[0], T->hi[0], T->nb[0]);
+    case OR_T_DQ: {
+      /* elastic momentum transfer Q = 2 k sin(theta/2), k = 2 pi / lambda (Eq. eQelastic) */
+      double Q = 4.0 * PI * sin(0.5 * tally_angle(T, r)) / lambda;
+      return bin1(Q, T->lo[0], T->hi[0], T->nb[0]);
     }
     case OR_T_PSD: {
       int bx = bin1(r[0], T->lo[0], T->hi[0], T->nb[0]);
@@ -404,7 +414,7 @@ static void score(ctx* c, const particle* P, int trigger, int volume, int face) 
     if (T->trigger != trigger || T->volume != volume) continue;
     if (T->face >= 0 && T->face != face) continue;
     if (T->scat >= 0 && T->scat != P->nscat) continue;
-    int b = tally_bin(T, P->r, P->lambda);
+    int b = tally_bin(T, P->r, P->lambda, P->nscat);
     if (b < 0) continue;
     int idx = c->tally_off[t] + b;
     int tb = or_total_bins(s);

@@ -41,7 +41,7 @@ extern "C" {
 enum { OR_BOX = 0, OR_TUBE = 1, OR_SPHERE = 2 };
 enum { OR_ROLE_BULK = 0, OR_ROLE_DETECTOR = 1, OR_ROLE_BLACK = 2 };
 enum { OR_P_ABS = 0, OR_P_INC = 1, OR_P_BRAGG = 2, OR_NPROC = 3 };
-enum { OR_T_COUNT = 0, OR_T_ANGULAR = 1, OR_T_PSD = 2, OR_T_WLX = 3 };
+enum { OR_T_COUNT = 0, OR_T_ANGULAR = 1, OR_T_PSD = 2, OR_T_WLX = 3, OR_T_MULTISCAT = 4, OR_T_DQ = 5 };
 enum { OR_PTS_ENTRY = 0, OR_PTS_EXIT = 1 };
 enum { OR_PAR_RADIUS = 0, OR_PAR_SCALE = 1, OR_PAR_DENSITY = 2 };
 enum { OR_SRC_PENCIL = 0, OR_SRC_RECT = 1 };

@@ -22,7 +22,7 @@ LIB = HERE / "liboracle.so"
 MAX_PAR = 4
 _SHAPES = {"box": 0, "tube": 1, "sphere": 2}
 _ROLES = {"bulk": 0, "detector": 1, "black": 2}
-_TALLY = {"count": 0, "angular": 1, "psd": 2, "wlx": 3}
+_TALLY = {"count": 0, "angular": 1, "psd": 2, "wlx": 3, "multiscat": 4, "dq": 5}
 _PTS = {"entry": 0, "exit": 1}
 _PAR = {"radius": 0, "scale": 1, "density": 2}
 END_NAMES = ["escaped", "absorbed", "detected", "black", "mirror", "truncated", "aperture", "lost"]

@@ -800,14 +800,15 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
   long long tb = 0;
   for (int t = 0; t < d->n_tallies; ++t) {
     const tp_tally_desc& T = s->tallies[t];
-    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_WLX) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: kind", t));
+    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_DQ) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: kind", t));
     if (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: trigger", t));
     if (T.volume < -1 || T.volume >= d->n_prims) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: volume %d", t, T.volume));
     if (T.volume == -1 && T.trigger == TP_PTS_ENTRY) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: the world has no ENTRY", t));
     if (T.nbins[0] < 1 || T.nbins[1] < 1) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: bins", t));
     if (T.kind == TP_TALLY_COUNT && (T.nbins[0] != 1 || T.nbins[1] != 1)) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: a count has one bin", t));
-    if (T.kind == TP_TALLY_ANGULAR && T.nbins[1] != 1) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: angular is 1-D", t));
-    const int dims = (T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) ? 2 : (T.kind == TP_TALLY_ANGULAR ? 1 : 0);
+    if ((T.kind == TP_TALLY_ANGULAR || T.kind == TP_TALLY_MULTISCAT || T.kind == TP_TALLY_DQ) && T.nbins[1] != 1)
+      return bail(fail(TP_ERR_INVALID_ARG, "tally %d: a 1-D scorer has nbins[1] = 1", t));
+    const int dims = (T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) ? 2 : (T.kind == TP_TALLY_COUNT ? 0 : 1);
     for (int k = 0; k < dims; ++k)
       if (!(T.hi[k] > T.lo[k]) || !std::isfinite(T.hi[k]) || !std::isfinite(T.lo[k]))
         return bail(fail(TP_ERR_INVALID_ARG, "tally %d: range of axis %d", t, k));
@@ -1235,7 +1236,7 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   long long tb = 0;
   for (int t = 0; t < d->n_tallies; ++t) {
     const tp_tally_desc& T = s.tallies[t];
-    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_WLX || (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) ||
+    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_DQ || (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) ||
         T.volume < -1 || T.volume >= d->n_prims || (T.volume == -1 && T.trigger == TP_PTS_ENTRY) ||
         T.nbins[0] < 1 || T.nbins[1] < 1 || (T.kind != TP_TALLY_COUNT && !(T.hi[0] > T.lo[0])) ||
         ((T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) && !(T.hi[1] > T.lo[1])))

@@ -499,17 +499,27 @@ __device__ __forceinline__ int bin1(R x, R lo, R hi, R inv_w, int n) {
   return (b >= 0 && b < n) ? b : (b >= n ? n - 1 : -1);
 }
 
+// angle between (x - origin) and the tally axis, accurate at small angles
 template <typename R>
-__device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam) {
+__device__ __forceinline__ R tally_angle(const DTally<R>& T, R x0, R x1, R x2) {
+  const R v0 = x0 - T.origin[0], v1 = x1 - T.origin[1], v2 = x2 - T.origin[2];
+  const R dt = v0 * T.axis[0] + v1 * T.axis[1] + v2 * T.axis[2];
+  const R c0 = v1 * T.axis[2] - v2 * T.axis[1], c1 = v2 * T.axis[0] - v0 * T.axis[2],
+          c2 = v0 * T.axis[1] - v1 * T.axis[0];
+  return d_atan2(d_sqrt(c0 * c0 + c1 * c1 + c2 * c2), dt);
+}
+
+template <typename R>
+__device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam, int nscat) {
   switch (T.kind) {
     case TP_TALLY_COUNT: return 0;
-    case TP_TALLY_ANGULAR: {
-      const R v0 = x0 - T.origin[0], v1 = x1 - T.origin[1], v2 = x2 - T.origin[2];
-      const R dt = v0 * T.axis[0] + v1 * T.axis[1] + v2 * T.axis[2];
-      const R c0 = v1 * T.axis[2] - v2 * T.axis[1], c1 = v2 * T.axis[0] - v0 * T.axis[2],
-              c2 = v0 * T.axis[1] - v1 * T.axis[0];
-      const R th = d_atan2(d_sqrt(c0 * c0 + c1 * c1 + c2 * c2), dt);
-      return bin1(th, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    case TP_TALLY_ANGULAR: return bin1(tally_angle(T, x0, x1, x2), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    case TP_TALLY_MULTISCAT: return bin1((R)nscat, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    case TP_TALLY_DQ: {
+      // elastic momentum transfer Q = 4 pi sin(theta/2) / lambda (Eq. eQelastic)
+      R sh, ch;
+      d_sincos(R(0.5) * tally_angle(T, x0, x1, x2), &sh, &ch);
+      return bin1(Tr<R>::kFourPi * sh / lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
     }
     case TP_TALLY_PSD: {
       const int bx = bin1(x0, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
@@ -538,7 +548,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     const DTally<R>& T = tallies[t];
     if (T.face >= 0 && T.face != face) continue;
     if (T.scat >= 0 && T.scat != nscat) continue;
-    const int b = tally_bin(T, x0, x1, x2, lam);
+    const int b = tally_bin(T, x0, x1, x2, lam, nscat);
     if (b < 0) continue;
     const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
     const double w = (double)w_;

@@ -17,7 +17,7 @@ from . import native as N
 _SHAPES = {"box": N.TP_BOX, "tube": N.TP_TUBE, "sphere": N.TP_SPHERE}
 _ROLES = {"bulk": N.TP_ROLE_BULK, "detector": N.TP_ROLE_DETECTOR, "black": N.TP_ROLE_BLACK}
 _TALLY = {"count": N.TP_TALLY_COUNT, "angular": N.TP_TALLY_ANGULAR, "psd": N.TP_TALLY_PSD,
-          "wlx": N.TP_TALLY_WLX}
+          "wlx": N.TP_TALLY_WLX, "multiscat": N.TP_TALLY_MULTISCAT, "dq": N.TP_TALLY_DQ}
 _PTS = {"entry": N.TP_PTS_ENTRY, "exit": N.TP_PTS_EXIT}
 _PAR = {"radius": N.TP_PAR_RADIUS, "scale": N.TP_PAR_SCALE, "density": N.TP_PAR_DENSITY}
 

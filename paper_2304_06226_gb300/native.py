@@ -16,7 +16,7 @@ STATUS_NAMES = ["TP_OK", "TP_ERR_INVALID_ARG", "TP_ERR_GEOMETRY", "TP_ERR_CUDA",
 TP_BOX, TP_TUBE, TP_SPHERE = 0, 1, 2
 TP_ROLE_BULK, TP_ROLE_DETECTOR, TP_ROLE_BLACK = 0, 1, 2
 TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3
-TP_TALLY_COUNT, TP_TALLY_ANGULAR, TP_TALLY_PSD, TP_TALLY_WLX = 0, 1, 2, 3
+TP_TALLY_COUNT, TP_TALLY_ANGULAR, TP_TALLY_PSD, TP_TALLY_WLX, TP_TALLY_MULTISCAT, TP_TALLY_DQ = 0, 1, 2, 3, 4, 5
 TP_PTS_ENTRY, TP_PTS_EXIT = 0, 1
 TP_PAR_RADIUS, TP_PAR_SCALE, TP_PAR_DENSITY = 0, 1, 2
 TP_SRC_PENCIL, TP_SRC_RECT = 0, 1

@@ -372,3 +372,32 @@ def test_event_cap_truncates_and_counts_like_the_oracle(eng, orc, kernel):
     o = orc.OracleScene(desc).run(n)
     assert gpu["counters"]["truncated"] == o["counters"]["truncated"] > 1000
     assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Per-scattering-order scorers (MultiScat, DeltaMomentum)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_total_scattering_fp64_matches_oracle(eng, orc, kernel):
+    n = 30_000
+    desc = W.total_scattering(g=3.0, n_histories=n, precision="f64")
+    gpu = gpu_run(eng, desc, n, kernel=kernel)
+    o = orc.OracleScene(desc).run(n)
+    assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(gpu["raw"]["sumsq"], o["sumsq"], rtol=1e-9, atol=1e-12)
+
+
+def test_total_scattering_fp32_and_conservation_per_order(eng, orc):
+    n = 4_000_000
+    runs = {}
+    for g in (1.0, 3.0):
+        desc = W.total_scattering(g=g, n_histories=n)
+        raw = gpu_run(eng, desc, n, seed=4096 + int(g))["raw"]
+        runs[g] = stats(raw["sum"], raw["sumsq"], n)
+    ok, info = compare_tallies(*runs[1.0], *runs[3.0])
+    assert ok, info
+    desc = W.total_scattering(g=1.0, n_histories=n)
+    o = orc.OracleScene(desc).run(n // 4)
+    m2, e2 = stats(o["sum"], o["sumsq"], n // 4)
+    ok, info = compare_tallies(*runs[1.0], m2, e2)
+    assert ok, info

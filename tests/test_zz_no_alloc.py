@@ -35,7 +35,7 @@ def marshal(N, desc):
     keep = []
     shapes = {"box": N.TP_BOX, "tube": N.TP_TUBE, "sphere": N.TP_SPHERE}
     roles = {"bulk": 0, "detector": 1, "black": 2}
-    kinds = {"count": 0, "angular": 1, "psd": 2, "wlx": 3}
+    kinds = {"count": 0, "angular": 1, "psd": 2, "wlx": 3, "multiscat": 4, "dq": 5}
     prims, mirrors = desc["prims"], []
     P = (N.tp_prim * max(1, len(prims)))()
     for i, p in enumerate(prims):

@@ -313,5 +313,34 @@ def imaging(n_histories: int = 1_000_000_000, precision: str = "f32", n_prims: i
                   n_histories, instances=inst, params=pdesc)
 
 
+# ----------------------------------------------------------------------------
+# Total scattering with per-scattering-order tallies (stand-in for §4.1)
+# ----------------------------------------------------------------------------
+def total_scattering(g: float = 1.0, n_histories: int = 10_000_000, precision: str = "f32",
+                     radius: float = 1.2, lam: float = 1.0, max_order: int = 3, nq: int = 200):
+    """Pencil beam of wavelength `lam` on a sphere of radius `radius` cm of the
+    synthetic fcc powder (Bragg lines + incoherent 0.3/cm) inside a 4 pi
+    spherical detector shell (radius 200 cm); bias g on every process of the
+    sample.  Tallies: the scattering-number spectrum (MultiScat) and the
+    elastic momentum transfer Q of all neutrons and of those scattered exactly
+    1 .. max_order times (DeltaMomentum with its scatnum filter)."""
+    world = {"shape": BOX, "centre": (0.0, 0.0, 0.0), "params": (250.0, 250.0, 250.0)}
+    lines = fcc_bragg_lines()
+    prims = [prim(SPHERE, (0, 0, 0), (0.0, radius, 0.0), material=0),
+             prim(SPHERE, (0, 0, 0), (200.0, 201.0, 0.0), role="detector")]
+    mats = [material(sigma_abs_ref=0.05, abs_mode="1/v", sigma_inc=0.3, bragg=lines)]
+    source = {"kind": "pencil", "centre": (0.0, 0.0, -100.0), "half": (0.0, 0.0),
+              "lambda": (lam, lam), "div": (0.0, 0.0), "aperture": None}
+    qmax = 4 * math.pi / lam
+    tallies = [tally("multiscat", "entry", 1, bins=(8, 1), lo=(0.0, 0.0), hi=(8.0, 1.0),
+                     name="scattering_number")]
+    for order in [-1] + list(range(1, max_order + 1)):
+        tallies.append(tally("dq", "entry", 1, bins=(nq, 1), lo=(0.0, 0.0), hi=(qmax, 1.0),
+                             origin=(0, 0, 0), axis=(0, 0, 1), scat=order,
+                             name="Q_all" if order < 0 else f"Q_{order}"))
+    return _scene("total_scattering", world, prims, mats, [[g, g, g]], source, tallies,
+                  precision, n_histories)
+
+
 WORKLOADS = {"slab": slab, "powder": powder, "guide": guide, "batched": batched,
-             "imaging": imaging}
+             "imaging": imaging, "total_scattering": total_scattering}
