@@ -1175,13 +1175,14 @@ __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KP
 // Event-based persistent kernel: a bank of neutrons in shared memory, one slot
 // per thread, regrouped every event by what each neutron needs next.  Every
 // iteration builds, with warp ballots, one queue per event type -- new history,
-// advance inside a primitive, advance in the world region, crossing out of a
-// primitive, crossing into one, collision -- and runs the queues one after
-// the other with consecutive threads taking consecutive entries, so that the
-// warps of a phase all run the same code.
+// advance inside a primitive, advance in the world region, collision -- and
+// runs the queues one after the other with consecutive threads taking
+// consecutive entries, so that the warps of a phase all run the same code.  An
+// advance that reaches a boundary crosses it in the same pass (inside a
+// primitive every crossing is an exit, in the world region an entry).
 // ---------------------------------------------------------------------------
-enum { EV_EMPTY = 0, EV_ADV = 1, EV_XEXIT = 2, EV_XENT = 3, EV_COLL = 4 };
-enum { Q_EMPTY = 0, Q_ADVP, Q_ADVW, Q_XEXIT, Q_XENT, Q_COLL, kNumQ };
+enum { EV_EMPTY = 0, EV_ADV = 1, EV_COLL = 2 };
+enum { Q_EMPTY = 0, Q_ADVP, Q_ADVW, Q_COLL, kNumQ };
 
 // Append `slot` to queue q if `pred`; all lanes of the warp must call this.
 __device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pred, int slot) {
@@ -1202,10 +1203,6 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
   *dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
 }
 
-template <typename R>
-__device__ __forceinline__ int pend_of(int type, int face, int target) {
-  return type | ((face + 1) << 4) | ((target + 4) << 8);
-}
 
 template <typename R, bool GRAD, bool GRID>
 __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__ KParams<R> kp) {
@@ -1254,8 +1251,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
     if (tid < kNumQ) qcount[tid] = 0;
     __syncthreads();
     {
-      const int pe = pend[tid];
-      const int ty = pe & 15;
+      const int ty = pend[tid];
       q_push(qlist + Q_EMPTY * NB, &qcount[Q_EMPTY], ty == EV_EMPTY, tid);
       bool inprim = false;
       if (ty == EV_ADV) inprim = bank[tid].vol >= 0;
@@ -1310,66 +1306,45 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
     __syncthreads();
     const int n_advp = qcount[Q_ADVP], n_advw = qcount[Q_ADVW];
     if (n_advp + n_advw == 0 && claim_state == 1) break;   // uniform: shared values
-    // ---- advance: inside primitives, then in the world region ----
+    // ---- advance, then cross at once (inside primitives every crossing is an
+    //      exit, in the world region an entry); collisions are queued ----
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       const int n = pass == 0 ? n_advp : n_advw;
       const unsigned short* L = qlist + (pass == 0 ? Q_ADVP : Q_ADVW) * NB;
-      int slot = 0, out = -1;
+      int slot = 0;
+      bool coll = false;
       if (tid < n) {
         slot = L[tid];
         Particle<R> P = bank[slot];
         R ip[kMaxPar], dR;
         load_params(kp, P.inst, ip, &dR);
         Adv<R> a;
-        out = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
-        if (out == kOutCross) {
-          pend[slot] = pend_of<R>(P.vol >= 0 ? EV_XEXIT : EV_XENT, a.face, a.target);
-        } else if (out == kOutColl) {
+        int end = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
+        bool spawn = false;
+        Particle<R> S;
+        if (end == kOutCross) end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        if (end == kOutColl) {
           pend[slot] = EV_COLL;
+          coll = true;
         } else {
-          finish(kp, P, out);
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
+          if (end >= 0) finish(kp, P, end);
+          if (GRAD && spawn) {
+            if (end < 0) { park[slot] = P; parked[slot] = 1; }
+            P = S;
+            pend[slot] = EV_ADV;
+          } else if (end >= 0) {
+            if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+            else pend[slot] = EV_EMPTY;
+          } else {
+            pend[slot] = EV_ADV;
+          }
         }
         bank[slot] = P;
       }
-      const bool is_cross = out == kOutCross;
-      const bool exitp = is_cross && (pend[slot] & 15) == EV_XEXIT;
-      q_push(qlist + Q_XEXIT * NB, &qcount[Q_XEXIT], tid < n && is_cross && exitp, slot);
-      q_push(qlist + Q_XENT * NB, &qcount[Q_XENT], tid < n && is_cross && !exitp, slot);
-      q_push(qlist + Q_COLL * NB, &qcount[Q_COLL], tid < n && out == kOutColl, slot);
+      q_push(qlist + Q_COLL * NB, &qcount[Q_COLL], tid < n && coll, slot);
     }
     __syncthreads();
-    // ---- crossings: out of primitives, then into primitives / world exit ----
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      const int n = qcount[pass == 0 ? Q_XEXIT : Q_XENT];
-      const unsigned short* L = qlist + (pass == 0 ? Q_XEXIT : Q_XENT) * NB;
-      if (tid < n) {
-        const int slot = L[tid];
-        Particle<R> P = bank[slot];
-        const int pe = pend[slot];
-        const int face = ((pe >> 4) & 15) - 1, target = (pe >> 8) - 4;
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        Particle<R> S;
-        bool spawn = false;
-        const int end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, face, target, &S, &spawn);
-        if (end >= 0) finish(kp, P, end);
-        if (GRAD && spawn) {
-          if (end < 0) { park[slot] = P; parked[slot] = 1; }
-          P = S;
-          pend[slot] = EV_ADV;
-        } else if (end >= 0) {
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
-        } else {
-          pend[slot] = EV_ADV;
-        }
-        bank[slot] = P;
-      }
-    }
     // ---- collisions ----
     {
       const int n = qcount[Q_COLL];
@@ -1405,9 +1380,10 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
 // ---------------------------------------------------------------------------
 // Warp-pool kernel: each warp owns kPool neutrons in shared memory and, every
 // step, runs the event type most of them wait for (new history, advance in a
-// primitive, advance in the world, exit crossing, entry crossing, collision) on
-// up to 32 of them, so the warp executes one code path with most lanes busy.
-// Warps never wait for one another: no CTA barrier after the table copy.
+// primitive -- with the exit crossing --, advance in the world -- with the
+// entry crossing --, collision) on up to 32 of them, so the warp executes one
+// code path with most lanes busy.  Warps never wait for one another: no CTA
+// barrier after the table copy.
 // ---------------------------------------------------------------------------
 #ifndef TP_POOL
 #define TP_POOL 64
@@ -1459,23 +1435,21 @@ __global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__
 
   for (;;) {
     // ---- count what the pool waits for ----
-    unsigned m[6][kPoolGroups];
+    unsigned m[kNumQ][kPoolGroups];
 #pragma unroll
     for (int g = 0; g < kPoolGroups; ++g) {
       const int slot = g * 32 + lane;
-      const int ty = pend[slot] & 15;
+      const int ty = pend[slot];
       const bool adv = ty == EV_ADV;
       const bool inprim = adv && pool[slot].vol >= 0;
       m[Q_EMPTY][g] = __ballot_sync(kFull, ty == EV_EMPTY);
       m[Q_ADVP][g] = __ballot_sync(kFull, adv && inprim);
       m[Q_ADVW][g] = __ballot_sync(kFull, adv && !inprim);
-      m[Q_XEXIT][g] = __ballot_sync(kFull, ty == EV_XEXIT);
-      m[Q_XENT][g] = __ballot_sync(kFull, ty == EV_XENT);
       m[Q_COLL][g] = __ballot_sync(kFull, ty == EV_COLL);
     }
-    int count[6];
+    int count[kNumQ];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < kNumQ; ++q) {
       count[q] = 0;
 #pragma unroll
       for (int g = 0; g < kPoolGroups; ++g) count[q] += __popc(m[q][g]);
@@ -1487,7 +1461,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__
     } else {
       int best = 0;
 #pragma unroll
-      for (int k = 1; k < 6; ++k)
+      for (int k = 1; k < kNumQ; ++k)
         if (count[k] > best) { best = count[k]; q = k; }
       if (q < 0) {
         if (work_left && count[Q_EMPTY] > 0) q = Q_EMPTY;
@@ -1547,43 +1521,32 @@ __global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__
         taken += avail;
       }
     } else if (q == Q_ADVP || q == Q_ADVW) {
+      // advance, and cross at once: inside a primitive every crossing is an
+      // exit, in the world region an entry, so the lanes stay on one path;
+      // collisions wait in their own queue
       if (slot >= 0) {
         Particle<R> P = pool[slot];
         R ip[kMaxPar], dR;
         load_params(kp, P.inst, ip, &dR);
         Adv<R> a;
-        const int out = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
-        if (out == kOutCross) {
-          pend[slot] = pend_of<R>(P.vol >= 0 ? EV_XEXIT : EV_XENT, a.face, a.target);
-        } else if (out == kOutColl) {
+        int end = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
+        bool spawn = false;
+        Particle<R> S;
+        if (end == kOutCross) end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        if (end == kOutColl) {
           pend[slot] = EV_COLL;
         } else {
-          finish(kp, P, out);
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
-        }
-        pool[slot] = P;
-      }
-    } else if (q == Q_XEXIT || q == Q_XENT) {
-      if (slot >= 0) {
-        Particle<R> P = pool[slot];
-        const int pe = pend[slot];
-        const int face = ((pe >> 4) & 15) - 1, target = (pe >> 8) - 4;
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        Particle<R> S;
-        bool spawn = false;
-        const int end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, face, target, &S, &spawn);
-        if (end >= 0) finish(kp, P, end);
-        if (GRAD && spawn) {
-          if (end < 0) { park[slot] = P; parked[slot] = 1; }
-          P = S;
-          pend[slot] = EV_ADV;
-        } else if (end >= 0) {
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
-        } else {
-          pend[slot] = EV_ADV;
+          if (end >= 0) finish(kp, P, end);
+          if (GRAD && spawn) {
+            if (end < 0) { park[slot] = P; parked[slot] = 1; }
+            P = S;
+            pend[slot] = EV_ADV;
+          } else if (end >= 0) {
+            if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+            else pend[slot] = EV_EMPTY;
+          } else {
+            pend[slot] = EV_ADV;
+          }
         }
         pool[slot] = P;
       }
