@@ -38,7 +38,7 @@ POWDER_N = 100_000_000
 INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638, "batched": 13454}
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
-TRAFFIC_PER_LAUNCH = {("powder", 3): 324352 + 11930368, ("powder", 1): 634880 + 68608}
+TRAFFIC_PER_LAUNCH = {("powder", 3): 827648 + 247808, ("batched", 2): 59525888 + 31343104}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1}
@@ -319,7 +319,8 @@ def run_batched(args, W, Scene, torch) -> dict:
     return {"value": hist_s, "unit": UNIT, "instances": int(len(counts)), "histories_per_step": total,
             "launch": launch,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
-                         "frac": achieved / peak, "traffic": None, "per_unit": INST_PER_HISTORY["batched"],
+                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("batched", launch["kernel"])),
+                         "per_unit": INST_PER_HISTORY["batched"],
                          "kernel": "transport forward with score-function accumulators"},
             "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
             "rel_stderr_total_median_instance": rel,
