@@ -802,7 +802,11 @@ struct Adv {
   int face, target;   // crossing: face id; target primitive, -3 = leaving the world
 };
 
-template <typename R, bool GRAD, bool GRID>
+// WHERE: kAny, or kInPrim / kInWorld when the caller knows where the neutron
+// is (the regrouping kernels), which drops the other branch from the code.
+constexpr int kAny = 0, kInPrim = 1, kInWorld = 2;
+
+template <typename R, bool GRAD, bool GRID, int WHERE = kAny>
 __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
                        unsigned long long* cnt, Adv<R>& a) {
   const R INF = Tr<R>::inf();
@@ -810,7 +814,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   if ((int)P.k > kp.event_cap) { cnt[C_TRUNC]++; return END_TRUNCATED; }
   cnt[C_EVENTS]++;
   a.r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
-  const int mat = P.vol >= 0 ? V.prims[P.vol].material : -1;
+  const int mat = (WHERE == kInWorld) ? -1 : (P.vol >= 0 ? V.prims[P.vol].material : -1);
   R* sig = a.sig;
   sig[0] = sig[1] = sig[2] = R(0);
   R sig_t = R(0), sig_g = R(0);
@@ -825,7 +829,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   // next boundary
   R db;
   int target = -3, face = -1;
-  if (P.vol >= 0) {
+  if (WHERE == kInPrim || (WHERE == kAny && P.vol >= 0)) {
     db = exit_dist(V.prims[P.vol], dR, P.x, P.u, &face);
   } else {
     db = world_exit(kp, P.x, P.u);
@@ -868,11 +872,11 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
 
 // Relocation at the boundary reached by advance (face / target of `a`).
 // spawn: set when a radius-derivative secondary was created into *S.
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, int WHERE = kAny>
 __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
                      unsigned long long* cnt, int face, int target, Particle<R>* S, bool* spawn) {
   cnt[C_CROSS]++;
-  if (P.vol >= 0) {
+  if (WHERE == kInPrim || (WHERE == kAny && P.vol >= 0)) {
     // leave the current primitive: EXIT scorers, then relocate
     const int from = P.vol;
     const DPrim<R>& pf = V.prims[from];
@@ -1320,10 +1324,16 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
         R ip[kMaxPar], dR;
         load_params(kp, P.inst, ip, &dR);
         Adv<R> a;
-        int end = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
         bool spawn = false;
         Particle<R> S;
-        if (end == kOutCross) end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        int end;
+        if (pass == 0) {
+          end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
+          if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        } else {
+          end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
+          if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        }
         if (end == kOutColl) {
           pend[slot] = EV_COLL;
           coll = true;
@@ -1529,10 +1539,16 @@ __global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__
         R ip[kMaxPar], dR;
         load_params(kp, P.inst, ip, &dR);
         Adv<R> a;
-        int end = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
         bool spawn = false;
         Particle<R> S;
-        if (end == kOutCross) end = cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        int end;
+        if (q == Q_ADVP) {
+          end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
+          if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        } else {
+          end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
+          if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+        }
         if (end == kOutColl) {
           pend[slot] = EV_COLL;
         } else {
