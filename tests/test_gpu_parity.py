@@ -401,3 +401,18 @@ def test_total_scattering_fp32_and_conservation_per_order(eng, orc):
     m2, e2 = stats(o["sum"], o["sumsq"], n // 4)
     ok, info = compare_tallies(*runs[1.0], m2, e2)
     assert ok, info
+
+
+def test_absorption_bias_on_gpu_matches_unbiased_and_oracle(eng, orc):
+    n = 2_000_000
+    base = gpu_run(eng, W.imaging(n_histories=n, n_prims=300, psd_bins=16, g_thin=1.0), n)["raw"]
+    desc = W.imaging(n_histories=n, n_prims=300, psd_bins=16, g_thin=1.0, abs_bias=0.1)
+    biased = gpu_run(eng, desc, n, seed=99)["raw"]
+    m1, e1 = stats(base["sum"], base["sumsq"], n)
+    m2, e2 = stats(biased["sum"], biased["sumsq"], n)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    o = orc.OracleScene(desc).run(n // 4)
+    m3, e3 = stats(o["sum"], o["sumsq"], n // 4)
+    ok, info = compare_tallies(m2, e2, m3, e3)
+    assert ok, info

@@ -64,3 +64,39 @@ def test_biased_and_unbiased_agree_per_scattering_order(oracle_mod, threads):
     (m1, e1), (m3, e3) = res
     ok, info = compare_tallies(m1, e1, m3, e3)
     assert ok, info
+
+
+def test_absorption_bias_conserves_and_smooths_the_image(oracle_mod, threads):
+    """§4.4: with abs_bias = 0.1 the transmission image is the same and less noisy."""
+    n = 300_000
+    out = {}
+    for ab in (None, 0.1):
+        d = W.imaging(n_histories=n, n_prims=150, psd_bins=8, abs_bias=ab, g_thin=1.0)
+        r = oracle_mod.OracleScene(d).run(n, threads=threads)
+        out[ab] = stats(r["sum"], r["sumsq"], n)
+    (m1, e1), (m2, e2) = out[None], out[0.1]
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    # implicit capture never adds noise (here the pixel choice dominates the noise)
+    assert np.median(e2 / np.maximum(e1, 1e-300)) < 1.0
+
+
+@pytest.mark.parametrize("g", [0.1, 0.5, 1.0])
+def test_absorption_bias_second_moment_closed_form(oracle_mod, threads, g):
+    """Pure absorber of optical depth S t with absorption bias g: a history
+    passes with probability exp(-g S t) carrying w = exp((g-1) S t), so
+    E[w] = exp(-S t) and E[w^2] = exp((g-2) S t) exactly."""
+    n = 400_000
+    S = 0.5
+    d = W.slab(g=1.0, n_histories=n, sigma_s=0.0, sigma_a=S)
+    d["bias"][0] = [g, 1.0, 1.0]
+    r = oracle_mod.OracleScene(d).run(n, threads=threads)
+    m1 = r["sum"][1] / n
+    m2 = r["sumsq"][1] / n
+    e1 = math.sqrt(max(m2 - m1 * m1, 0) / n)
+    assert abs(m1 - math.exp(-S)) < 4 * e1 + 1e-12
+    expect2 = math.exp((g - 2) * S)
+    # the second moment's own standard error: w^2 takes one value
+    w2 = math.exp(2 * (g - 1) * S)
+    e2 = w2 * math.sqrt(math.exp(-g * S) * (1 - math.exp(-g * S)) / n)
+    assert abs(m2 - expect2) < 4 * e2 + 1e-12, (m2, expect2)

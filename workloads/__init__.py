@@ -288,7 +288,7 @@ def imaging_primitives(n: int = 1000, half: float = 5.0, seed: int = SEED_SCENE,
 
 
 def imaging(n_histories: int = 1_000_000_000, precision: str = "f32", n_prims: int = 1000,
-            g_thin: float = 5.0, psd_bins: int = 512, seed: int = SEED_SCENE):
+            g_thin: float = 5.0, psd_bins: int = 512, seed: int = SEED_SCENE, abs_bias: float = None):
     """1000 random primitives in a 10 cm cube, 3 materials with Sigma_t
     (0.2, 1, 3)/cm and scatter fractions (0.9, 0.5, 0.1) (constant absorption),
     parallel 10 x 10 cm beam lambda ~ U(0.5, 6) A, bias 5 on the thinnest
@@ -302,6 +302,10 @@ def imaging(n_histories: int = 1_000_000_000, precision: str = "f32", n_prims: i
     mats = [material(sigma_abs_ref=(1 - f) * s, abs_mode="const", sigma_inc=f * s,
                      density_param=i) for i, (s, f) in enumerate(zip(sig_t, frac))]
     bias = [[g_thin] * 3, [1.0] * 3, [1.0] * 3]
+    if abs_bias is not None:
+        # separate absorption bias (the abs_bias of §3.5, 0.1 in the §4.4 imaging study)
+        for b in bias:
+            b[ABS] = abs_bias
     source = {"kind": "rect", "centre": (0.0, 0.0, -6.0), "half": (5.0, 5.0),
               "lambda": (0.5, 6.0), "div": (0.0, 0.0), "aperture": None}
     tallies = [tally("psd", "entry", len(prims) - 1, bins=(psd_bins, psd_bins),
