@@ -65,9 +65,10 @@ enum { TP_TALLY_COUNT = 0, TP_TALLY_ANGULAR = 1, TP_TALLY_PSD = 2, TP_TALLY_WLX 
 enum { TP_PTS_ENTRY = 0, TP_PTS_EXIT = 1 };
 /* Differentiable instance parameters. */
 enum { TP_PAR_RADIUS = 0, TP_PAR_SCALE = 1, TP_PAR_DENSITY = 2 };
-/* Particle guns (§3.2): a pencil (SimpleThermalGun with a fixed direction) and a
- * rectangle emitting along +z (a moderator surface, UniModeratorGun-like). */
-enum { TP_SRC_PENCIL = 0, TP_SRC_RECT = 1 };
+/* Particle guns (§3.2): a pencil (SimpleThermalGun with a fixed direction), a
+ * rectangle emitting along +z with uniform divergence, and a moderator
+ * rectangle aiming at a slit (UniModeratorGun / MaxwellianGun). */
+enum { TP_SRC_PENCIL = 0, TP_SRC_RECT = 1, TP_SRC_MODERATOR = 2 };
 /* Transport arithmetic. */
 enum { TP_FP32 = 0, TP_FP64 = 1 };
 
@@ -115,8 +116,16 @@ typedef struct {
 
 /* Source.  TP_SRC_PENCIL: at centre, direction +z.  TP_SRC_RECT: uniform on the
  * rectangle centre +- half (x, y), direction +z tilted by angles uniform in
- * +-div (x, y).  Wavelength uniform on [lambda_lo, lambda_hi].  With
- * has_aperture, neutrons born outside centre +- aperture are stopped. */
+ * +-div (x, y).  TP_SRC_MODERATOR: uniform on the rectangle centre +- half
+ * (x, y) at z = centre[2], aimed at a point uniform on the slit rectangle
+ * (centre.x, centre.y) +- slit_half at z = slit_z (> centre[2]).
+ * Wavelength uniform on [lambda_lo, lambda_hi], or, if temperature > 0, from
+ * the Maxwell-Boltzmann energy distribution sqrt(E) exp(-E/kT) at that
+ * temperature (K); a Maxwellian source with an angular divergence must be
+ * TP_SRC_MODERATOR (the two would share random numbers otherwise), and
+ * tp_create_scene rejects the combination with TP_ERR_INVALID_ARG.  With
+ * has_aperture, neutrons born outside centre +- aperture are stopped.
+ * (§3.2: ParticleGun, UniModeratorGun, MaxwellianGun.) */
 typedef struct {
   int kind;
   double centre[3];
@@ -125,6 +134,9 @@ typedef struct {
   double div[2];
   int has_aperture;
   double aperture[2];
+  double slit_z;
+  double slit_half[2];
+  double temperature;
 } tp_source;
 
 /* Scene description.  The world is a vacuum box (params = half extents) or

@@ -729,12 +729,29 @@ static void history(ctx* c, uint64_t hid, or_record* rec) {
   draw4(s, 0u, 1u, hid, c->inst, b);
   const or_source* g = &s->src;
   P.r[0] = g->c[0]; P.r[1] = g->c[1]; P.r[2] = g->c[2];
-  if (g->kind == OR_SRC_RECT) {
+  if (g->kind == OR_SRC_RECT || g->kind == OR_SRC_MODERATOR) {
     P.r[0] += g->half[0] * (2.0 * a[0] - 1.0);
     P.r[1] += g->half[1] * (2.0 * a[1] - 1.0);
   }
-  P.lambda = (g->lam_hi > g->lam_lo) ? g->lam_lo + (g->lam_hi - g->lam_lo) * a[2] : g->lam_lo;
-  if (g->div[0] > 0.0 || g->div[1] > 0.0) {
+  if (g->temperature > 0.0) {
+    /* MaxwellianGun (§3.2): kinetic energy from the Maxwell-Boltzmann
+     * distribution sqrt(E) exp(-E/kT), i.e. E/kT ~ Gamma(3/2): the sum of an
+     * exponential variate and half the square of a normal one, the latter by
+     * the Box-Muller construction; then lambda = sqrt((h^2/2m_n) / E). */
+    const double kT = 0.08617333 * g->temperature;          /* meV */
+    const double c = cos(0.5 * PI * b[3]);
+    const double E = kT * (-log(a[2]) - log(a[3]) * c * c);   /* meV */
+    P.lambda = sqrt(81.80420 / E);                           /* A */
+  } else {
+    P.lambda = (g->lam_hi > g->lam_lo) ? g->lam_lo + (g->lam_hi - g->lam_lo) * a[2] : g->lam_lo;
+  }
+  if (g->kind == OR_SRC_MODERATOR) {
+    /* UniModeratorGun / MaxwellianGun: aim at a point uniform on the slit */
+    double t[3] = {g->c[0] + g->slit_half[0] * (2.0 * b[1] - 1.0) - P.r[0],
+                   g->c[1] + g->slit_half[1] * (2.0 * b[2] - 1.0) - P.r[1], g->slit_z - P.r[2]};
+    double n = sqrt(dot3(t, t));
+    P.u[0] = t[0] / n; P.u[1] = t[1] / n; P.u[2] = t[2] / n;
+  } else if (g->div[0] > 0.0 || g->div[1] > 0.0) {
     double tx = tan(g->div[0] * (2.0 * a[3] - 1.0));
     double ty = tan(g->div[1] * (2.0 * b[0] - 1.0));
     double n = sqrt(tx * tx + ty * ty + 1.0);

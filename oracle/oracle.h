@@ -44,7 +44,7 @@ enum { OR_P_ABS = 0, OR_P_INC = 1, OR_P_BRAGG = 2, OR_NPROC = 3 };
 enum { OR_T_COUNT = 0, OR_T_ANGULAR = 1, OR_T_PSD = 2, OR_T_WLX = 3, OR_T_MULTISCAT = 4, OR_T_DQ = 5 };
 enum { OR_PTS_ENTRY = 0, OR_PTS_EXIT = 1 };
 enum { OR_PAR_RADIUS = 0, OR_PAR_SCALE = 1, OR_PAR_DENSITY = 2 };
-enum { OR_SRC_PENCIL = 0, OR_SRC_RECT = 1 };
+enum { OR_SRC_PENCIL = 0, OR_SRC_RECT = 1, OR_SRC_MODERATOR = 2 };
 /* how a history ended */
 enum { OR_END_ESCAPED = 0, OR_END_ABSORBED = 1, OR_END_DETECTED = 2, OR_END_BLACK = 3,
        OR_END_MIRROR = 4, OR_END_TRUNCATED = 5, OR_END_APERTURE = 6, OR_END_LOST = 7 };
@@ -84,6 +84,9 @@ typedef struct {
   double div[2];
   int has_aperture;
   double aperture[2];
+  double slit_z;        /* moderator gun: slit plane and half sizes */
+  double slit_half[2];
+  double temperature;   /* > 0: Maxwell-Boltzmann energies at this temperature (K) */
 } or_source;
 
 typedef struct {

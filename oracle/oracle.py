@@ -72,7 +72,8 @@ class Tally(C.Structure):
 class Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("c", C.c_double * 3), ("half", C.c_double * 2),
                 ("lam_lo", C.c_double), ("lam_hi", C.c_double), ("div", C.c_double * 2),
-                ("has_aperture", C.c_int), ("aperture", C.c_double * 2)]
+                ("has_aperture", C.c_int), ("aperture", C.c_double * 2), ("slit_z", C.c_double),
+                ("slit_half", C.c_double * 2), ("temperature", C.c_double)]
 
 
 class Scene(C.Structure):
@@ -195,10 +196,13 @@ class OracleScene:
         self._keep.append(bias)
         src = desc["source"]
         ap = src.get("aperture")
-        S = Source(1 if src["kind"] == "rect" else 0, (C.c_double * 3)(*src["centre"]),
+        if src.get("temperature", 0.0) > 0 and src["kind"] != "moderator" and max(src["div"]) > 0:
+            raise ValueError("a Maxwellian source with divergence must be a moderator gun")
+        S = Source({"pencil": 0, "rect": 1, "moderator": 2}[src["kind"]], (C.c_double * 3)(*src["centre"]),
                    (C.c_double * 2)(*src["half"]), src["lambda"][0], src["lambda"][1],
                    (C.c_double * 2)(*src["div"]), 1 if ap else 0,
-                   (C.c_double * 2)(*(ap if ap else (0.0, 0.0))))
+                   (C.c_double * 2)(*(ap if ap else (0.0, 0.0))), float(src.get("slit_z", 0.0)),
+                   (C.c_double * 2)(*src.get("slit_half", (0.0, 0.0))), float(src.get("temperature", 0.0)))
         tallies = desc["tallies"]
         T = (Tally * max(1, len(tallies)))()
         for i, t in enumerate(tallies):

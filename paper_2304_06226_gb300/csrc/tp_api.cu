@@ -45,6 +45,23 @@ bool finite_all(const double* v, int n) {
   return true;
 }
 
+constexpr double kBoltzmann_meV = 0.08617333;   // k_B in meV/K
+
+// Source checks shared by both ways of describing a scene.
+bool source_ok(const tp_source& src) {
+  if (src.kind < TP_SRC_PENCIL || src.kind > TP_SRC_MODERATOR) return false;
+  if (!(src.temperature >= 0) || !std::isfinite(src.temperature)) return false;
+  if (src.temperature == 0 && (!(src.lambda_lo > 0) || !(src.lambda_hi >= src.lambda_lo) || !std::isfinite(src.lambda_hi)))
+    return false;
+  if (!(src.div[0] >= 0 && src.div[0] < 1.5 && src.div[1] >= 0 && src.div[1] < 1.5)) return false;
+  if (src.temperature > 0 && src.kind != TP_SRC_MODERATOR && (src.div[0] > 0 || src.div[1] > 0)) return false;
+  if (src.kind == TP_SRC_MODERATOR &&
+      (!(src.slit_z > src.centre[2]) || !(src.slit_half[0] >= 0) || !(src.slit_half[1] >= 0) ||
+       !std::isfinite(src.slit_z) || !std::isfinite(src.slit_half[0]) || !std::isfinite(src.slit_half[1])))
+    return false;
+  return finite_all(src.centre, 3) && finite_all(src.half, 2);
+}
+
 struct Mat {
   tp_material m;
   std::vector<double> d, mult, F2;  // sorted by d descending
@@ -527,6 +544,10 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   }
   k.src_lam_lo = (R)src.lambda_lo;
   k.src_lam_hi = (R)src.lambda_hi;
+  k.src_slit_z = (R)src.slit_z;
+  k.src_slit_half[0] = (R)src.slit_half[0];
+  k.src_slit_half[1] = (R)src.slit_half[1];
+  k.src_kT = (R)(kBoltzmann_meV * src.temperature);
   k.event_cap = s->event_cap;
   k.use_grid = s->grid_cells > 0 ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
@@ -789,12 +810,10 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
       return bail(fail(TP_ERR_INVALID_ARG, "mirror %d: need R0, Qc, alpha, m >= 0 and W > 0", i));
   }
   // source
-  const tp_source& src = s->source;
-  if (src.kind != TP_SRC_PENCIL && src.kind != TP_SRC_RECT) return bail(fail(TP_ERR_INVALID_ARG, "source kind %d", src.kind));
-  if (!(src.lambda_lo > 0) || !(src.lambda_hi >= src.lambda_lo) || !std::isfinite(src.lambda_hi))
-    return bail(fail(TP_ERR_INVALID_ARG, "source wavelength range"));
-  if (!(src.div[0] >= 0 && src.div[0] < 1.5 && src.div[1] >= 0 && src.div[1] < 1.5))
-    return bail(fail(TP_ERR_INVALID_ARG, "source divergence must be in [0, 1.5) rad"));
+  if (!source_ok(s->source))
+    return bail(fail(TP_ERR_INVALID_ARG, "source: kind, wavelength range (> 0, lo <= hi) or temperature (>= 0), "
+                                         "divergence in [0, 1.5) rad (none with a temperature unless "
+                                         "TP_SRC_MODERATOR), slit beyond the moderator"));
   // tallies
   s->tally_off.resize(s->tallies.size() + 1);
   long long tb = 0;
@@ -1227,11 +1246,7 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
     const tp_mirror& m = s.mirrors[i];
     if (!(m.R0 >= 0 && m.Qc >= 0 && m.W > 0 && m.alpha >= 0 && m.m >= 0)) return fail(TP_ERR_INVALID_ARG, "mirror %d", i);
   }
-  const tp_source& src = s.source;
-  if ((src.kind != TP_SRC_PENCIL && src.kind != TP_SRC_RECT) || !(src.lambda_lo > 0) ||
-      !(src.lambda_hi >= src.lambda_lo) || !std::isfinite(src.lambda_hi) ||
-      !(src.div[0] >= 0 && src.div[0] < 1.5 && src.div[1] >= 0 && src.div[1] < 1.5))
-    return fail(TP_ERR_INVALID_ARG, "source");
+  if (!source_ok(s.source)) return fail(TP_ERR_INVALID_ARG, "source");
   s.tally_off.resize(s.tallies.size() + 1);
   long long tb = 0;
   for (int t = 0; t < d->n_tallies; ++t) {

@@ -43,6 +43,7 @@ template <> struct Tr<float> {
   }
   static __device__ __forceinline__ float nudge(float m) { return 1e-5f * fmaxf(1.0f, m); }
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+  static constexpr float kPi = 3.14159265358979323846f;
   static constexpr float kTwoPi = 6.283185307179586f;
   static constexpr float kFourPi = 12.566370614359172f;
 };
@@ -52,9 +53,13 @@ template <> struct Tr<double> {
   }
   static __device__ __forceinline__ double nudge(double m) { return 1e-9 * fmax(1.0, m); }
   static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+  static constexpr double kPi = 3.14159265358979323846;
   static constexpr double kTwoPi = 6.283185307179586;
   static constexpr double kFourPi = 12.566370614359172;
 };
+
+// h^2 / (2 m_n) in meV A^2: E = kH2over2mn / lambda^2
+constexpr double kH2over2mn = 81.80420;
 
 __device__ __forceinline__ float d_log(float x) { return logf(x); }
 __device__ __forceinline__ double d_log(double x) { return log(x); }
@@ -583,14 +588,33 @@ template <typename R>
 __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R dR, int* end) {
   const uint4 a = philox(make_uint4(0u, 0u, P.hid, P.inst), kp.key0, kp.key1);
   P.x[0] = kp.src_c[0]; P.x[1] = kp.src_c[1]; P.x[2] = kp.src_c[2];
-  if (kp.src_kind == TP_SRC_RECT) {
+  if (kp.src_kind != TP_SRC_PENCIL) {
     P.x[0] += kp.src_half[0] * (R(2) * Tr<R>::u01(a.x) - R(1));
     P.x[1] += kp.src_half[1] * (R(2) * Tr<R>::u01(a.y) - R(1));
   }
-  P.lam = kp.src_lam_hi > kp.src_lam_lo ? kp.src_lam_lo + (kp.src_lam_hi - kp.src_lam_lo) * Tr<R>::u01(a.z)
-                                        : kp.src_lam_lo;
-  if (kp.src_div[0] > R(0) || kp.src_div[1] > R(0)) {
-    const uint4 b = philox(make_uint4(0u, 1u, P.hid, P.inst), kp.key0, kp.key1);
+  const bool need_b = kp.src_kind == TP_SRC_MODERATOR || kp.src_kT > R(0) || kp.src_div[0] > R(0) ||
+                      kp.src_div[1] > R(0);
+  uint4 b = make_uint4(0u, 0u, 0u, 0u);
+  if (need_b) b = philox(make_uint4(0u, 1u, P.hid, P.inst), kp.key0, kp.key1);
+  if (kp.src_kT > R(0)) {
+    // Maxwell-Boltzmann energies sqrt(E) exp(-E/kT): E/kT ~ Gamma(3/2) = an
+    // exponential variate plus half a squared normal one (Box-Muller)
+    R sc, cc;
+    d_sincos(R(0.5) * Tr<R>::kPi * Tr<R>::u01(b.w), &sc, &cc);
+    const R e = kp.src_kT * (-d_log(Tr<R>::u01(a.z)) - d_log(Tr<R>::u01(a.w)) * cc * cc);
+    P.lam = d_sqrt(R(kH2over2mn) / e);
+  } else {
+    P.lam = kp.src_lam_hi > kp.src_lam_lo ? kp.src_lam_lo + (kp.src_lam_hi - kp.src_lam_lo) * Tr<R>::u01(a.z)
+                                          : kp.src_lam_lo;
+  }
+  if (kp.src_kind == TP_SRC_MODERATOR) {
+    // towards a point uniform on the slit
+    const R d0 = kp.src_c[0] + kp.src_slit_half[0] * (R(2) * Tr<R>::u01(b.y) - R(1)) - P.x[0];
+    const R d1 = kp.src_c[1] + kp.src_slit_half[1] * (R(2) * Tr<R>::u01(b.z) - R(1)) - P.x[1];
+    const R d2 = kp.src_slit_z - P.x[2];
+    const R inv = R(1) / d_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    P.u[0] = d0 * inv; P.u[1] = d1 * inv; P.u[2] = d2 * inv;
+  } else if (kp.src_div[0] > R(0) || kp.src_div[1] > R(0)) {
     const R tx = d_tan(kp.src_div[0] * (R(2) * Tr<R>::u01(a.w) - R(1)));
     const R ty = d_tan(kp.src_div[1] * (R(2) * Tr<R>::u01(b.x) - R(1)));
     const R inv = R(1) / d_sqrt(tx * tx + ty * ty + R(1));

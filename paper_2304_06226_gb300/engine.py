@@ -22,6 +22,17 @@ _PTS = {"entry": N.TP_PTS_ENTRY, "exit": N.TP_PTS_EXIT}
 _PAR = {"radius": N.TP_PAR_RADIUS, "scale": N.TP_PAR_SCALE, "density": N.TP_PAR_DENSITY}
 
 
+_SRC = {"pencil": N.TP_SRC_PENCIL, "rect": N.TP_SRC_RECT, "moderator": N.TP_SRC_MODERATOR}
+
+
+def source_struct(src: dict) -> N.tp_source:
+    ap = src.get("aperture")
+    return N.tp_source(_SRC[src["kind"]], N.D3(*src["centre"]), N.D2(*src["half"]), src["lambda"][0],
+                       src["lambda"][1], N.D2(*src["div"]), 1 if ap else 0,
+                       N.D2(*(ap if ap else (0.0, 0.0))), float(src.get("slit_z", 0.0)),
+                       N.D2(*src.get("slit_half", (0.0, 0.0))), float(src.get("temperature", 0.0)))
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -49,11 +60,7 @@ class Scene:
         M = (N.tp_mirror * max(1, len(mirrors)))()
         for i, m in enumerate(mirrors):
             M[i] = N.tp_mirror(m["m"], m["R0"], m["Qc"], m["alpha"], m["W"])
-        src = desc["source"]
-        ap = src.get("aperture")
-        S = N.tp_source(N.TP_SRC_RECT if src["kind"] == "rect" else N.TP_SRC_PENCIL,
-                        N.D3(*src["centre"]), N.D2(*src["half"]), src["lambda"][0], src["lambda"][1],
-                        N.D2(*src["div"]), 1 if ap else 0, N.D2(*(ap if ap else (0.0, 0.0))))
+        S = source_struct(desc["source"])
         tallies = desc["tallies"]
         T = (N.tp_tally_desc * max(1, len(tallies)))()
         for i, t in enumerate(tallies):

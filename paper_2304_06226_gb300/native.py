@@ -19,7 +19,7 @@ TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3
 TP_TALLY_COUNT, TP_TALLY_ANGULAR, TP_TALLY_PSD, TP_TALLY_WLX, TP_TALLY_MULTISCAT, TP_TALLY_DQ = 0, 1, 2, 3, 4, 5
 TP_PTS_ENTRY, TP_PTS_EXIT = 0, 1
 TP_PAR_RADIUS, TP_PAR_SCALE, TP_PAR_DENSITY = 0, 1, 2
-TP_SRC_PENCIL, TP_SRC_RECT = 0, 1
+TP_SRC_PENCIL, TP_SRC_RECT, TP_SRC_MODERATOR = 0, 1, 2
 TP_FP32, TP_FP64 = 0, 1
 TP_KERNEL_AUTO, TP_KERNEL_HISTORY, TP_KERNEL_EVENT, TP_KERNEL_WARPQ = 0, 1, 2, 3
 TP_MAX_PARAMS = 4
@@ -53,7 +53,8 @@ class tp_tally_desc(C.Structure):
 class tp_source(C.Structure):
     _fields_ = [("kind", C.c_int), ("centre", D3), ("half", D2), ("lambda_lo", C.c_double),
                 ("lambda_hi", C.c_double), ("div", D2), ("has_aperture", C.c_int),
-                ("aperture", D2)]
+                ("aperture", D2), ("slit_z", C.c_double), ("slit_half", D2),
+                ("temperature", C.c_double)]
 
 
 class tp_scene_desc(C.Structure):

@@ -50,7 +50,8 @@ def test_struct_layout_matches_header(native, tmp_path):
 def _desc(native, **kw):
     N = native
     prims = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, N.D3(0, 0, 0.5), N.D3(5, 5, 0.5)))
-    src = N.tp_source(N.TP_SRC_PENCIL, N.D3(0, 0, -1), N.D2(0, 0), 1.8, 1.8, N.D2(0, 0), 0, N.D2(0, 0))
+    src = N.tp_source(N.TP_SRC_PENCIL, N.D3(0, 0, -1), N.D2(0, 0), 1.8, 1.8, N.D2(0, 0), 0, N.D2(0, 0),
+                      0.0, N.D2(0, 0), 0.0)
     tallies = (N.tp_tally_desc * 1)(N.tp_tally_desc(N.TP_TALLY_COUNT, N.TP_PTS_EXIT, 0, 5, -1, N.I2(1, 1),
                                                     N.D2(0, 0), N.D2(1, 1), N.D3(0, 0, 0), N.D3(0, 0, 1)))
     d = N.tp_scene_desc(N.TP_SPHERE, N.D3(0, 0, 0.5), N.D3(0, 100, 0), 1, prims, 0, None, src, 1, tallies,

@@ -416,3 +416,31 @@ def test_absorption_bias_on_gpu_matches_unbiased_and_oracle(eng, orc):
     m3, e3 = stats(o["sum"], o["sumsq"], n // 4)
     ok, info = compare_tallies(m2, e2, m3, e3)
     assert ok, info
+
+
+# ---------------------------------------------------------------------------
+# Moderator guns (UniModeratorGun, MaxwellianGun)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("T", [None, 293.15])
+def test_moderator_guns_fp64_match_oracle_history_by_history(eng, orc, kernel, T):
+    n = 20_000
+    for z in (0.0, 40.0):
+        desc = W.moderator_test(n_histories=n, precision="f64", temperature=T, detector_z=z)
+        gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
+        o = orc.OracleScene(desc).run(n, records=True)
+        assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+        assert np.allclose(gpu["records"]["final_pos"], o["records"]["final_pos"], rtol=1e-9, atol=1e-9)
+        assert (gpu["records"]["end"] == o["records"]["end"]).all()
+
+
+@pytest.mark.parametrize("T", [None, 293.15])
+def test_moderator_guns_fp32_statistics(eng, orc, T):
+    n = 4_000_000
+    desc = W.moderator_test(n_histories=n, temperature=T, detector_z=40.0)
+    raw = gpu_run(eng, desc, n)["raw"]
+    m1, e1 = stats(raw["sum"], raw["sumsq"], n)
+    o = orc.OracleScene(desc).run(n // 4)
+    m2, e2 = stats(o["sum"], o["sumsq"], n // 4)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info

@@ -49,8 +49,10 @@ def marshal(N, desc):
                                                 for m in mirrors])
     s = desc["source"]
     ap = s.get("aperture")
-    src = N.tp_source(1 if s["kind"] == "rect" else 0, N.D3(*s["centre"]), N.D2(*s["half"]), s["lambda"][0],
-                      s["lambda"][1], N.D2(*s["div"]), 1 if ap else 0, N.D2(*(ap or (0.0, 0.0))))
+    src = N.tp_source({"pencil": 0, "rect": 1, "moderator": 2}[s["kind"]], N.D3(*s["centre"]), N.D2(*s["half"]),
+                      s["lambda"][0], s["lambda"][1], N.D2(*s["div"]), 1 if ap else 0, N.D2(*(ap or (0.0, 0.0))),
+                      float(s.get("slit_z", 0.0)), N.D2(*s.get("slit_half", (0.0, 0.0))),
+                      float(s.get("temperature", 0.0)))
     T = (N.tp_tally_desc * max(1, len(desc["tallies"])))()
     for i, t in enumerate(desc["tallies"]):
         T[i] = N.tp_tally_desc(kinds[t["kind"]], 0 if t["trigger"] == "entry" else 1, t["volume"], t["face"],

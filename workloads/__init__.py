@@ -318,6 +318,38 @@ def imaging(n_histories: int = 1_000_000_000, precision: str = "f32", n_prims: i
 
 
 # ----------------------------------------------------------------------------
+# Moderator guns (§3.2: UniModeratorGun, MaxwellianGun)
+# ----------------------------------------------------------------------------
+def moderator_source(src_w=10.0, src_h=5.0, src_z=-40.0, slit_w=0.5, slit_h=1.0, slit_z=0.1,
+                     mean_wl=3.39, range_wl=0.3, temperature=None):
+    """Moderator rectangle (full sizes, cm) at src_z aiming at a slit at slit_z.
+    Wavelength uniform on [mean_wl - range_wl, mean_wl + range_wl] (the reading
+    of the UniModeratorGun listing, whose caption gives 3.09-3.69 A for 3.39 and
+    0.3), or Maxwellian at `temperature` (K)."""
+    lo, hi = mean_wl - range_wl, mean_wl + range_wl
+    return {"kind": "moderator", "centre": (0.0, 0.0, float(src_z)), "half": (src_w / 2, src_h / 2),
+            "lambda": (lo, hi), "div": (0.0, 0.0), "aperture": None, "slit_z": float(slit_z),
+            "slit_half": (slit_w / 2, slit_h / 2), "temperature": float(temperature or 0.0)}
+
+
+def moderator_test(n_histories=1_000_000, precision="f32", temperature=None, lam_bins=60,
+                   detector_z=0.0):
+    """An empty world with a moderator gun (moderator 10 x 5 cm at z = -40 cm,
+    slit 0.5 x 1 cm at z = 0) and a detector face at `detector_z` carrying a
+    PSD (40 x 40 bins over +-1 cm at the slit, +-8 cm further out) and a
+    wavelength spectrum (checks of the guns)."""
+    world = {"shape": BOX, "centre": (0.0, 0.0, 0.0), "params": (100.0, 100.0, 100.0)}
+    src = moderator_source(src_z=-40.0, slit_z=0.0, temperature=temperature)
+    prims = [prim(BOX, (0, 0, detector_z + 0.05), (20.0, 20.0, 0.05), role="detector")]
+    half = 1.0 if detector_z == 0.0 else 8.0
+    tallies = [tally("psd", "entry", 0, bins=(40, 40), lo=(-half, -half), hi=(half, half), name="slit_psd"),
+               tally("wlx", "entry", 0, bins=(lam_bins, 1), lo=(0.2, -10.0), hi=(8.2, 10.0),
+                     name="spectrum")]
+    return _scene("moderator", world, prims, [], np.zeros((0, NPROC)), src, tallies, precision,
+                  n_histories)
+
+
+# ----------------------------------------------------------------------------
 # Total scattering with per-scattering-order tallies (stand-in for §4.1)
 # ----------------------------------------------------------------------------
 def total_scattering(g: float = 1.0, n_histories: int = 10_000_000, precision: str = "f32",
@@ -347,4 +379,4 @@ def total_scattering(g: float = 1.0, n_histories: int = 10_000_000, precision: s
 
 
 WORKLOADS = {"slab": slab, "powder": powder, "guide": guide, "batched": batched,
-             "imaging": imaging, "total_scattering": total_scattering}
+             "imaging": imaging, "total_scattering": total_scattering, "moderator": moderator_test}
