@@ -270,6 +270,7 @@ double or_prim_entry(const or_scene* s, const or_prim* p, const double* ip,
 static double world_exit(const or_scene* s, const double r[3], const double u[3]) {
   or_prim w;
   memset(&w, 0, sizeof w);
+  w.mirror = w.chopper = -1;
   w.shape = s->world_shape;
   for (int i = 0; i < 3; ++i) { w.c[i] = s->world_c[i]; w.p[i] = s->world_p[i]; }
   w.axis = 2;
@@ -280,6 +281,7 @@ static double world_exit(const or_scene* s, const double r[3], const double u[3]
 static int world_inside(const or_scene* s, const double r[3]) {
   or_prim w;
   memset(&w, 0, sizeof w);
+  w.mirror = w.chopper = -1;
   w.shape = s->world_shape;
   for (int i = 0; i < 3; ++i) { w.c[i] = s->world_c[i]; w.p[i] = s->world_p[i]; }
   w.axis = 2;
@@ -362,8 +364,18 @@ static double tally_angle(const or_tally* T, const double r[3]) {
 
 /* Bin of tally t for a particle at r with wavelength lambda after nscat
  * scatterings, or -1. */
-static int tally_bin(const or_tally* T, const double r[3], double lambda, int nscat) {
+/* Time of flight (s) of a neutron born at t = 0 that has flown `path` cm at
+ * wavelength lambda (A): its speed is v = h / (m_n lambda), h / m_n =
+ * 3956.034 m^2/s per A of wavelength (CODATA h and m_n), i.e.
+ * 395603.4 cm/s at 1 A.  Every process here is elastic, so the speed is
+ * constant along a history. */
+static double time_of_flight(double path, double lambda) {
+  return path * lambda / 395603.4012;
+}
+
+static int tally_bin(const or_tally* T, const double r[3], double lambda, int nscat, double path) {
   switch (T->kind) {
+    case OR_T_TOF: return bin1(time_of_flight(path, lambda), T->lo[0], T->hi[0], T->nb[0]);
     case OR_T_COUNT: return 0;
     case OR_T_ANGULAR: return bin1(tally_angle(T, r), T->lo[0], T->hi[0], T->nb[0]);
     case OR_T_MULTISCAT: return bin1((double)nscat, T->lo[0], T->hi[0], T->nb[0]);
@@ -392,6 +404,7 @@ static int tally_bin(const or_tally* T, const double r[3], double lambda, int ns
 typedef struct {
   double r[3], u[3], lambda, w;
   double A[OR_MAX_PAR];
+  double path;        /* length flown since the source (cm), for the time of flight */
   int vol, nscat;
   int secondary;      /* 1 for a radius-derivative secondary */
   uint32_t sub0;      /* sub-stream of its events */
@@ -414,7 +427,7 @@ static void score(ctx* c, const particle* P, int trigger, int volume, int face) 
     if (T->trigger != trigger || T->volume != volume) continue;
     if (T->face >= 0 && T->face != face) continue;
     if (T->scat >= 0 && T->scat != P->nscat) continue;
-    int b = tally_bin(T, P->r, P->lambda, P->nscat);
+    int b = tally_bin(T, P->r, P->lambda, P->nscat, P->path);
     if (b < 0) continue;
     int idx = c->tally_off[t] + b;
     int tb = or_total_bins(s);
@@ -434,6 +447,32 @@ static void score(ctx* c, const particle* P, int trigger, int volume, int face) 
       c->acc->J2[(size_t)c->radius_par * tb + idx] += g * g;
     }
   }
+}
+
+/* Disk chopper in ray-tracing mode (§2.1, Eq. eRayTracing; §2.5 and §3.5,
+ * DiskChopper): the factor epsilon is 1 if, at the moment the neutron reaches
+ * the (infinitely thin) disk, its position lies in an opening window, else 0.
+ * In the plane of the disk, with in-plane axes e1 = axis+1, e2 = axis+2
+ * (cyclic) about the tube centre, the neutron is at radius rho and angle phi.
+ * At time t window k (k = 0..n-1) is centred at phase + 2 pi f t + 2 pi k / n
+ * and spans theta0; the disk is black for rho < r_black.  Written as the
+ * plain definition: the angular distance to each window centre in turn. */
+static int chopper_open(const or_scene* s, const or_prim* pt, const particle* P) {
+  const or_chopper* ch = &s->choppers[pt->chopper];
+  const int a1 = (pt->axis + 1) % 3, a2 = (pt->axis + 2) % 3;
+  const double q1 = P->r[a1] - pt->c[a1], q2 = P->r[a2] - pt->c[a2];
+  const double rho = sqrt(q1 * q1 + q2 * q2);
+  if (rho < ch->r_black) return 0;
+  const double phi = atan2(q2, q1);
+  const double t = time_of_flight(P->path, P->lambda);
+  for (int k = 0; k < ch->n; ++k) {
+    const double centre = ch->phase + 2.0 * PI * ch->freq * t + 2.0 * PI * k / ch->n;
+    double d = fmod(phi - centre, 2.0 * PI);          /* in (-2 pi, 2 pi) */
+    if (d > PI) d -= 2.0 * PI;
+    if (d < -PI) d += 2.0 * PI;
+    if (fabs(d) <= 0.5 * ch->theta0) return 1;
+  }
+  return 0;
 }
 
 static double nudge_len(const double r[3]) {
@@ -574,6 +613,7 @@ static void transport(ctx* c, particle* P, uint64_t hid, or_record* rec, uint32_
     if (!isfinite(x)) { end = OR_END_LOST; acc->counters[5]++; break; }
     /* move and compensate the weight, Eq. eWeight: exp(sum_i (g_i-1) Sigma_i x) */
     for (int i = 0; i < 3; ++i) P->r[i] += x * P->u[i];
+    P->path += x;
     P->w *= exp((sig_g - sig_t) * x);
     if (grad && mat >= 0 && !P->secondary) {
       for (int p = 0; p < s->npar; ++p) {
@@ -609,6 +649,7 @@ static void transport(ctx* c, particle* P, uint64_t hid, or_record* rec, uint32_
           score(c, P, OR_PTS_ENTRY, v, -1);
           if (pt->role == OR_ROLE_DETECTOR) { end = OR_END_DETECTED; break; }
           if (pt->role == OR_ROLE_BLACK) { end = OR_END_BLACK; break; }
+          if (pt->chopper >= 0 && !chopper_open(s, pt, P)) { end = OR_END_BLACK; break; }
         }
       } else if (target == -3) {
         score(c, P, OR_PTS_EXIT, -1, -1);
@@ -644,6 +685,7 @@ static void transport(ctx* c, particle* P, uint64_t hid, or_record* rec, uint32_
           score(c, P, OR_PTS_ENTRY, target, face);
           if (pt->role == OR_ROLE_DETECTOR) { end = OR_END_DETECTED; break; }
           if (pt->role == OR_ROLE_BLACK) { end = OR_END_BLACK; break; }
+          if (pt->chopper >= 0 && !chopper_open(s, pt, P)) { end = OR_END_BLACK; break; }
         }
       }
     } else {

@@ -41,7 +41,8 @@ extern "C" {
 enum { OR_BOX = 0, OR_TUBE = 1, OR_SPHERE = 2 };
 enum { OR_ROLE_BULK = 0, OR_ROLE_DETECTOR = 1, OR_ROLE_BLACK = 2 };
 enum { OR_P_ABS = 0, OR_P_INC = 1, OR_P_BRAGG = 2, OR_NPROC = 3 };
-enum { OR_T_COUNT = 0, OR_T_ANGULAR = 1, OR_T_PSD = 2, OR_T_WLX = 3, OR_T_MULTISCAT = 4, OR_T_DQ = 5 };
+enum { OR_T_COUNT = 0, OR_T_ANGULAR = 1, OR_T_PSD = 2, OR_T_WLX = 3, OR_T_MULTISCAT = 4, OR_T_DQ = 5,
+       OR_T_TOF = 6 };
 enum { OR_PTS_ENTRY = 0, OR_PTS_EXIT = 1 };
 enum { OR_PAR_RADIUS = 0, OR_PAR_SCALE = 1, OR_PAR_DENSITY = 2 };
 enum { OR_SRC_PENCIL = 0, OR_SRC_RECT = 1, OR_SRC_MODERATOR = 2 };
@@ -53,11 +54,18 @@ enum { OR_END_ESCAPED = 0, OR_END_ABSORBED = 1, OR_END_DETECTED = 2, OR_END_BLAC
 
 typedef struct {
   int shape, axis, material, role, mirror, bind_rmin, bind_rmax;
+  int chopper;      /* index into or_scene.choppers or -1 */
   double c[3];      /* centre */
   double p[3];      /* box: half extents; tube: rmin, rmax, half height; sphere: rmin, rmax, - */
 } or_prim;
 
 typedef struct { double m, R0, Qc, alpha, W; } or_mirror;
+
+/* Disk chopper (§3.5, Table tableDiskChopper) on a vacuum tube: black below
+ * radius r_black, n windows of full opening theta0 (rad) evenly spread over
+ * 2 pi, rotating at freq (Hz, right-hand rule about the tube axis), window 0
+ * at angle phase (rad) from the first in-plane axis at time zero. */
+typedef struct { double r_black; int n; double freq, theta0, phase; } or_chopper;
 
 typedef struct {
   double sig_abs_ref;   /* Sigma_a at 1.8 A (abs_1v) or constant */
@@ -94,6 +102,7 @@ typedef struct {
   double world_c[3], world_p[3];
   int nprim;   const or_prim* prims;
   int nmirror; const or_mirror* mirrors;
+  int nchopper; const or_chopper* choppers;
   int nmat;    const or_material* mats;
   const double* bias;          /* [nmat][3] */
   or_source src;

@@ -22,7 +22,7 @@ LIB = HERE / "liboracle.so"
 MAX_PAR = 4
 _SHAPES = {"box": 0, "tube": 1, "sphere": 2}
 _ROLES = {"bulk": 0, "detector": 1, "black": 2}
-_TALLY = {"count": 0, "angular": 1, "psd": 2, "wlx": 3, "multiscat": 4, "dq": 5}
+_TALLY = {"count": 0, "angular": 1, "psd": 2, "wlx": 3, "multiscat": 4, "dq": 5, "tof": 6}
 _PTS = {"entry": 0, "exit": 1}
 _PAR = {"radius": 0, "scale": 1, "density": 2}
 END_NAMES = ["escaped", "absorbed", "detected", "black", "mirror", "truncated", "aperture", "lost"]
@@ -48,7 +48,7 @@ def build(force: bool = False) -> Path:
 class Prim(C.Structure):
     _fields_ = [("shape", C.c_int), ("axis", C.c_int), ("material", C.c_int), ("role", C.c_int),
                 ("mirror", C.c_int), ("bind_rmin", C.c_int), ("bind_rmax", C.c_int),
-                ("c", C.c_double * 3), ("p", C.c_double * 3)]
+                ("chopper", C.c_int), ("c", C.c_double * 3), ("p", C.c_double * 3)]
 
 
 class Mirror(C.Structure):
@@ -61,6 +61,11 @@ class Material(C.Structure):
                 ("nlines", C.c_int), ("V0", C.c_double), ("d", C.POINTER(C.c_double)),
                 ("mult", C.POINTER(C.c_double)), ("F2", C.POINTER(C.c_double)),
                 ("density_par", C.c_int), ("scale_par", C.c_int)]
+
+
+class Chopper(C.Structure):
+    _fields_ = [("r_black", C.c_double), ("n", C.c_int), ("freq", C.c_double), ("theta0", C.c_double),
+                ("phase", C.c_double)]
 
 
 class Tally(C.Structure):
@@ -80,6 +85,7 @@ class Scene(C.Structure):
     _fields_ = [("world_shape", C.c_int), ("world_c", C.c_double * 3), ("world_p", C.c_double * 3),
                 ("nprim", C.c_int), ("prims", C.POINTER(Prim)),
                 ("nmirror", C.c_int), ("mirrors", C.POINTER(Mirror)),
+                ("nchopper", C.c_int), ("choppers", C.POINTER(Chopper)),
                 ("nmat", C.c_int), ("mats", C.POINTER(Material)),
                 ("bias", C.POINTER(C.c_double)), ("src", Source),
                 ("ntally", C.c_int), ("tallies", C.POINTER(Tally)),
@@ -162,19 +168,25 @@ class OracleScene:
         self.desc = desc
         self._keep = []
         prims = desc["prims"]
-        mirrors = []
+        mirrors, choppers = [], []
         P = (Prim * max(1, len(prims)))()
         for i, p in enumerate(prims):
-            mi = -1
+            mi = ci = -1
             if p.get("mirror"):
                 mi = len(mirrors)
                 mirrors.append(p["mirror"])
+            if p.get("chopper"):
+                ci = len(choppers)
+                choppers.append(p["chopper"])
             P[i] = Prim(_SHAPES[p["shape"]], p["axis"], p["material"], _ROLES[p["role"]], mi,
-                        int(p["bind_rmin"]), int(p["bind_rmax"]),
+                        int(p["bind_rmin"]), int(p["bind_rmax"]), ci,
                         (C.c_double * 3)(*p["centre"]), (C.c_double * 3)(*p["params"]))
         M = (Mirror * max(1, len(mirrors)))()
         for i, m in enumerate(mirrors):
             M[i] = Mirror(m["m"], m["R0"], m["Qc"], m["alpha"], m["W"])
+        CH = (Chopper * max(1, len(choppers)))()
+        for i, ch in enumerate(choppers):
+            CH[i] = Chopper(ch["r_black"], ch["n"], ch["freq"], ch["theta0"], ch["phase"])
         mats = desc["materials"]
         MA = (Material * max(1, len(mats)))()
         for i, m in enumerate(mats):
@@ -216,11 +228,11 @@ class OracleScene:
         inst = desc["instances"]
         self.scene = Scene(_SHAPES[w["shape"]], (C.c_double * 3)(*w["centre"]),
                            (C.c_double * 3)(*w["params"]), len(prims), P, len(mirrors), M,
-                           len(mats), MA, _dptr(bias), S, len(tallies), T, len(desc["params"]),
+                           len(choppers), CH, len(mats), MA, _dptr(bias), S, len(tallies), T, len(desc["params"]),
                            pk.ctypes.data_as(C.POINTER(C.c_int)),
                            float(inst.get("radius_nominal", 0.0)), desc["seed"] & (2**64 - 1),
                            int(desc["event_cap"]))
-        self._keep += [P, M, MA, T]
+        self._keep += [P, M, CH, MA, T]
         self.npar = len(desc["params"])
         self.total_bins = lib().or_total_bins(C.byref(self.scene))
         self.tally_bins = [t["bins"][0] * t["bins"][1] for t in tallies]

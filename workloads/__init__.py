@@ -75,7 +75,7 @@ def fcc_bragg_lines(a: float = 3.6, dmin: float = 0.5, seed: int = SEED_TABLE,
 # Helpers building plain dict descriptions
 # ----------------------------------------------------------------------------
 def prim(shape, centre, params, material=-1, role="bulk", axis=2, mirror=None,
-         bind_rmin=False, bind_rmax=False):
+         bind_rmin=False, bind_rmax=False, chopper=None):
     """One CSG primitive.  params: box -> half extents (hx,hy,hz); tube ->
     (rmin, rmax, half_height) along `axis`; sphere -> (rmin, rmax, 0).
     role: 'bulk' (transport inside), 'detector' (terminal: scored on entry, then
@@ -83,7 +83,15 @@ def prim(shape, centre, params, material=-1, role="bulk", axis=2, mirror=None,
     return {"shape": shape, "centre": tuple(float(c) for c in centre),
             "params": tuple(float(p) for p in params), "material": int(material),
             "role": role, "axis": int(axis), "mirror": mirror,
-            "bind_rmin": bool(bind_rmin), "bind_rmax": bool(bind_rmax)}
+            "bind_rmin": bool(bind_rmin), "bind_rmax": bool(bind_rmax), "chopper": chopper}
+
+
+def disk_chopper(r_black, n=4, freq=100.0, theta0_deg=20.0, phase_deg=0.0):
+    """DiskChopper parameters of §3.5 (Table tableDiskChopper): black inner
+    radius (cm), number of windows, rotation frequency (Hz), opening angle and
+    phase (given in degrees as in the table, stored in radians)."""
+    return {"r_black": float(r_black), "n": int(n), "freq": float(freq),
+            "theta0": math.radians(theta0_deg), "phase": math.radians(phase_deg)}
 
 
 def material(sigma_abs_ref=0.0, abs_mode="1/v", sigma_inc=0.0, bragg=None,
@@ -97,7 +105,8 @@ def material(sigma_abs_ref=0.0, abs_mode="1/v", sigma_inc=0.0, bragg=None,
 
 def tally(kind, trigger, volume, bins=(1, 1), lo=(0.0, 0.0), hi=(1.0, 1.0),
           origin=(0.0, 0.0, 0.0), axis=(0.0, 0.0, 1.0), face=-1, scat=-1, name=""):
-    """kind: 'count' | 'angular' | 'psd' (x,y) | 'wlx' (lambda, x).
+    """kind: 'count' | 'angular' | 'psd' (x,y) | 'wlx' (lambda, x) | 'multiscat' |
+    'dq' | 'tof' (time of flight in s).
     trigger: 'entry' | 'exit' (particle tracing states of §3.4).
     volume: primitive index or -1 for the world.  face: -1 any, else face id.
     scat: scattering-number filter (-1 any, n >= 0 exactly n scatters)."""
@@ -350,6 +359,52 @@ def moderator_test(n_histories=1_000_000, precision="f32", temperature=None, lam
 
 
 # ----------------------------------------------------------------------------
+# Disk chopper in ray-tracing mode with time-of-flight scorers (§4.5)
+# ----------------------------------------------------------------------------
+CHOPPER_DISTANCE = 1000.0   # cm from the gun to the chopper plane
+
+
+def chopper(n_histories: int = 10_000_000, precision: str = "f32", tof_bins: int = 1000,
+            tof_max: float = 0.025):
+    """The chopper study of §4.5: a 293 K MaxwellianGun with a 1 mm x 1 mm
+    opening aimed at a 45 mm x 45 mm opening 10 m away, where a disk chopper
+    (4 windows of 20 degrees, 100 Hz, inner radius 13 cm, outer 25 cm) turns.
+    The chopper plane is z = 0 (gun at z = -10 m) and the beam crosses the disk
+    at radius 19 cm, at 90 degrees from the first in-plane axis, so that a
+    window is centred on the beam at t = 0.  Time-of-flight scorers on the
+    chopper's ENTRY (just before it) and EXIT (just after it), 25 us bins."""
+    world = {"shape": BOX, "centre": (0.0, 0.0, -495.0), "params": (40.0, 40.0, 510.0)}
+    src = moderator_source(src_w=0.1, src_h=0.1, src_z=-CHOPPER_DISTANCE, slit_w=4.5, slit_h=4.5,
+                           slit_z=0.0, temperature=293.0)
+    disk = disk_chopper(r_black=13.0, n=4, freq=100.0, theta0_deg=20.0, phase_deg=0.0)
+    prims = [prim(TUBE, (0.0, -19.0, 0.0), (0.0, 25.0, 0.05), axis=2, chopper=disk)]
+    tallies = [tally("tof", "entry", 0, bins=(tof_bins, 1), lo=(0.0, 0.0), hi=(tof_max, 1.0), name="tof_before"),
+               tally("tof", "exit", 0, bins=(tof_bins, 1), lo=(0.0, 0.0), hi=(tof_max, 1.0), name="tof_after"),
+               tally("count", "exit", 0, name="transmitted")]
+    return _scene("chopper", world, prims, [], np.zeros((0, NPROC)), src, tallies, precision, n_histories)
+
+
+def chopper_pencil(n_histories: int = 400_000, precision: str = "f64", disk_centre=(-10.0, -16.0),
+                   phase_deg=17.0, lam=(1.0, 3.0), temperature=None, freq=100.0, tof_bins=200,
+                   tof_max=0.025):
+    """A pencil beam along +z from (0, 0, -10 m) through a disk chopper in the
+    plane z = 0 centred at `disk_centre` (x, y): the beam meets the disk at a
+    single radius and angle, so that the transmitted fraction and the
+    time-of-flight spectra have closed forms."""
+    world = {"shape": BOX, "centre": (0.0, 0.0, -495.0), "params": (60.0, 60.0, 510.0)}
+    src = {"kind": "pencil", "centre": (0.0, 0.0, -CHOPPER_DISTANCE), "half": (0.0, 0.0),
+           "lambda": (float(lam[0]), float(lam[1])), "div": (0.0, 0.0), "aperture": None,
+           "temperature": float(temperature or 0.0)}
+    disk = disk_chopper(r_black=13.0, n=4, freq=freq, theta0_deg=20.0, phase_deg=phase_deg)
+    prims = [prim(TUBE, (disk_centre[0], disk_centre[1], 0.0), (0.0, 25.0, 0.05), axis=2, chopper=disk)]
+    tallies = [tally("tof", "entry", 0, bins=(tof_bins, 1), lo=(0.0, 0.0), hi=(tof_max, 1.0), name="tof_before"),
+               tally("tof", "exit", 0, bins=(tof_bins, 1), lo=(0.0, 0.0), hi=(tof_max, 1.0), name="tof_after"),
+               tally("count", "exit", 0, name="transmitted")]
+    return _scene("chopper_pencil", world, prims, [], np.zeros((0, NPROC)), src, tallies, precision,
+                  n_histories)
+
+
+# ----------------------------------------------------------------------------
 # Total scattering with per-scattering-order tallies (stand-in for §4.1)
 # ----------------------------------------------------------------------------
 def total_scattering(g: float = 1.0, n_histories: int = 10_000_000, precision: str = "f32",
@@ -379,4 +434,5 @@ def total_scattering(g: float = 1.0, n_histories: int = 10_000_000, precision: s
 
 
 WORKLOADS = {"slab": slab, "powder": powder, "guide": guide, "batched": batched,
-             "imaging": imaging, "total_scattering": total_scattering, "moderator": moderator_test}
+             "imaging": imaging, "total_scattering": total_scattering, "moderator": moderator_test,
+             "chopper": chopper}
