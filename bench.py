@@ -35,13 +35,15 @@ POWDER_N = 100_000_000
 # ncu smsp__thread_inst_executed.sum / histories on a small case of each
 # workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
 # the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638, "batched": 13454}
+INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638, "batched": 13454,
+                    "chopper": 1880}
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
 TRAFFIC_PER_LAUNCH = {("powder", 3): 827648 + 247808, ("batched", 2): 59525888 + 31343104}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
-FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1}
+FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
+                "chopper": 2}
 SM_COUNT = 152
 LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -60,6 +62,9 @@ def workload_desc(name: str):
     if name == "total_scattering":
         return W.total_scattering(n_histories=100_000_000), ("total scattering: pencil on a 1.2 cm fcc-powder sphere, 4 pi "
                                                              "detector, Q per scattering order, 1e8 histories, FP32 transport")
+    if name == "chopper":
+        return W.chopper(n_histories=POWDER_N), ("disk chopper 4 x 20 deg at 100 Hz, 10 m from a 293 K MaxwellianGun, "
+                                                 "TOF before/after, 1e8 histories, FP32 transport")
     if name == "batched":
         return W.batched(), ("256 powder instances, uneven history counts (5.9e8 total), gradients w.r.t. "
                              "radius, scale, density + backward, FP32 transport")

@@ -57,10 +57,10 @@ enum { TP_ROLE_BULK = 0, TP_ROLE_DETECTOR = 1, TP_ROLE_BLACK = 2 };
 enum { TP_PROC_ABS = 0, TP_PROC_INC = 1, TP_PROC_BRAGG = 2, TP_NPROC = 3 };
 /* Scorers (§3.4, Table tableScorer): a count, Angular, PSD (x,y), a
  * wavelength x position monitor (WlSpectrum crossed with a PSD axis),
- * MultiScat (number of scatterings) and DeltaMomentum (elastic momentum
- * transfer, Eq. eQelastic). */
+ * MultiScat (number of scatterings), DeltaMomentum (elastic momentum
+ * transfer, Eq. eQelastic) and TOF (time of flight). */
 enum { TP_TALLY_COUNT = 0, TP_TALLY_ANGULAR = 1, TP_TALLY_PSD = 2, TP_TALLY_WLX = 3,
-       TP_TALLY_MULTISCAT = 4, TP_TALLY_DQ = 5 };
+       TP_TALLY_MULTISCAT = 4, TP_TALLY_DQ = 5, TP_TALLY_TOF = 6 };
 /* Particle tracing states that trigger scorers (§3.4). */
 enum { TP_PTS_ENTRY = 0, TP_PTS_EXIT = 1 };
 /* Differentiable instance parameters. */
@@ -83,9 +83,12 @@ enum { TP_FP32 = 0, TP_FP64 = 1 };
  * mirror: index into tp_scene_desc.mirrors or -1.  A neutron arriving at the
  *   boundary of a mirror primitive is reflected (§2.5) and never enters it.
  * bind_rmin / bind_rmax: the radius moves with the TP_PAR_RADIUS instance
- *   parameter, by (value - radius_nominal). */
+ *   parameter, by (value - radius_nominal).
+ * chopper: index into tp_scene_desc.choppers or -1.  The primitive is then a
+ *   vacuum (material -1) bulk TP_TUBE and no mirror: the disk of a chopper
+ *   (§3.5, DiskChopper), whose outer radius is the tube's rmax. */
 typedef struct {
-  int shape, axis, material, role, mirror, bind_rmin, bind_rmax;
+  int shape, axis, material, role, mirror, bind_rmin, bind_rmax, chopper;
   double centre[3];
   double params[3];
 } tp_prim;
@@ -94,6 +97,23 @@ typedef struct {
  * alpha (A), W (1/A). */
 typedef struct { double m, R0, Qc, alpha, W; } tp_mirror;
 
+/* Disk chopper in ray-tracing mode (§2.1, Eq. eRayTracing; §3.5, Table
+ * tableDiskChopper).  The disk is infinitely thin: a neutron entering its
+ * tube keeps its weight (epsilon = 1) if, at the entry point and time, it is
+ * at radius >= r_black from the tube axis and inside an opening window, and is
+ * stopped (epsilon = 0, end code "black") otherwise.  There are n_windows
+ * windows of full opening theta0 (rad), evenly spread over 2 pi, turning at
+ * freq (Hz; positive = right-hand rule about the tube axis); at time zero
+ * window 0 is centred at angle phase (rad) from the first in-plane axis
+ * (axis+1 mod 3, towards axis+2 mod 3).  Time is the time of flight since the
+ * source (see TP_TALLY_TOF).  ENTRY scorers of the tube see the neutron before
+ * the mask, EXIT scorers after it. */
+typedef struct {
+  double r_black;
+  int n_windows;
+  double freq, theta0, phase;
+} tp_chopper;
+
 /* A scorer.  kind TP_TALLY_ANGULAR bins the angle between (position - origin)
  * and axis over [lo[0], hi[0]) in nbins[0] bins; TP_TALLY_PSD bins x over
  * [lo[0],hi[0]) and y over [lo[1],hi[1]); TP_TALLY_WLX bins the wavelength over
@@ -101,7 +121,11 @@ typedef struct { double m, R0, Qc, alpha, W; } tp_mirror;
  * scatterings over [lo[0], hi[0]); TP_TALLY_DQ bins Q = 4 pi sin(theta/2)/lambda
  * (1/A) over [lo[0], hi[0]), theta being the angle between (position - origin)
  * and axis (origin = sample position, axis = beam direction: the elastic
- * momentum transfer of Eq. eQelastic).  Bins are laid out axis-0 major.
+ * momentum transfer of Eq. eQelastic); TP_TALLY_TOF bins the time of flight
+ * t (s) over [lo[0], hi[0]): sources emit at t = 0 and a neutron that has flown
+ * a path L (cm) at wavelength lambda (A) is at t = L lambda / 395603.4 (its
+ * speed h / (m_n lambda); every process is elastic).  Bins are laid out
+ * axis-0 major.
  * trigger TP_PTS_ENTRY / TP_PTS_EXIT of `volume` (primitive index, -1 = world).
  * face: -1 any, else the face id (box 2*axis + (1 for the + face); tube 0
  *   outer, 1 inner, 2 -cap, 3 +cap; sphere 0 outer, 1 inner).
@@ -155,6 +179,7 @@ typedef struct {
   double radius_nominal;
   int precision;   /* TP_FP32 | TP_FP64 */
   int event_cap;   /* events per history before it is truncated (counted); 0 = 4096 */
+  int n_choppers;  const tp_chopper* choppers;
 } tp_scene_desc;
 
 /* Creates a scene: validates the description (TP_ERR_INVALID_ARG,

@@ -80,6 +80,7 @@ struct tp_scene {
   double world_c[3] = {0, 0, 0}, world_p[3] = {0, 0, 0};
   std::vector<tp_prim> prims;
   std::vector<tp_mirror> mirrors;
+  std::vector<tp_chopper> choppers;
   tp_source source{};
   std::vector<tp_tally_desc> tallies;
   std::vector<int> tally_off;
@@ -94,8 +95,8 @@ struct tp_scene {
   uint8_t* d_blob = nullptr;
   size_t blob_cap = 0;
   uint32_t blob_bytes = 0;
-  uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_tallies = 0, off_line_d = 0, off_line_cum = 0,
-           off_nb = 0;
+  uint32_t off_prims = 0, off_mats = 0, off_mirrors = 0, off_choppers = 0, off_tallies = 0, off_line_d = 0,
+           off_line_cum = 0, off_nb = 0;
   bool blob_dirty = true;
   // uniform grid (scenes with more than kGridMinPrims primitives)
   int* d_grid = nullptr;   // [ncells + 1] starts, then items
@@ -328,7 +329,7 @@ void neighbours(const tp_scene* s, std::vector<double>& bound, std::vector<int>&
 template <typename R>
 std::vector<uint8_t> build_blob(tp_scene* s) {
   const int np = (int)s->prims.size(), nm = (int)s->mats.size(), nmir = (int)s->mirrors.size(),
-            nt = (int)s->tallies.size();
+            nch = (int)s->choppers.size(), nt = (int)s->tallies.size();
   int nl = 0;
   for (const auto& m : s->mats) nl += (int)m.d.size();
   std::vector<double> bound;
@@ -338,6 +339,7 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
   s->off_prims = (uint32_t)off; off = align16(off + sizeof(DPrim<R>) * np);
   s->off_mats = (uint32_t)off; off = align16(off + sizeof(DMat<R>) * std::max(nm, 1));
   s->off_mirrors = (uint32_t)off; off = align16(off + sizeof(DMirror<R>) * std::max(nmir, 1));
+  s->off_choppers = (uint32_t)off; off = align16(off + sizeof(DChopper<R>) * std::max(nch, 1));
   s->off_tallies = (uint32_t)off; off = align16(off + sizeof(DTally<R>) * std::max(nt, 1));
   s->off_line_d = (uint32_t)off; off = align16(off + sizeof(R) * std::max(nl, 1));
   s->off_line_cum = (uint32_t)off; off = align16(off + sizeof(R) * (nl + std::max(nm, 1)));
@@ -351,6 +353,7 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
     for (int k = 0; k < 3; ++k) { d.c[k] = (R)p.centre[k]; d.p[k] = (R)p.params[k]; }
     d.shape = p.shape; d.axis = p.axis; d.material = p.material; d.role = p.role;
     d.mirror = p.mirror; d.flags = (p.bind_rmin ? F_BIND_RMIN : 0) | (p.bind_rmax ? F_BIND_RMAX : 0);
+    if (p.chopper >= 0) d.flags |= F_CHOPPER | (p.chopper << kChopperShift);
     d.entry_mask = 0; d.exit_mask = 0;
     d.bound_r = (R)bound[i];
     d.nb_off = nb_off[i];
@@ -393,6 +396,13 @@ std::vector<uint8_t> build_blob(tp_scene* s) {
   for (int i = 0; i < nmir; ++i) {
     const tp_mirror& m = s->mirrors[i];
     MI[i] = DMirror<R>{(R)m.m, (R)m.R0, (R)m.Qc, (R)m.alpha, (R)m.W, (R)(m.m * m.Qc), R(0), R(0)};
+  }
+  auto* CH = reinterpret_cast<DChopper<R>*>(blob.data() + s->off_choppers);
+  for (int i = 0; i < nch; ++i) {
+    const tp_chopper& c = s->choppers[i];
+    const double n = c.n_windows, two_pi = 2.0 * M_PI;
+    CH[i] = DChopper<R>{(R)(c.r_black * c.r_black), (R)(n / two_pi), (R)(n * c.freq), (R)(n * c.phase / two_pi),
+                        (R)(n * c.theta0 / (2.0 * two_pi)), R(0), R(0), R(0)};
   }
   auto* T = reinterpret_cast<DTally<R>*>(blob.data() + s->off_tallies);
   for (int t = 0; t < nt; ++t) {
@@ -512,6 +522,7 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.blob = s->d_blob;
   k.blob_bytes = s->blob_bytes;
   k.off_prims = s->off_prims; k.off_mats = s->off_mats; k.off_mirrors = s->off_mirrors;
+  k.off_choppers = s->off_choppers;
   k.off_tallies = s->off_tallies; k.off_line_d = s->off_line_d; k.off_line_cum = s->off_line_cum;
   k.off_nb = s->off_nb;
   k.stage_blob = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
@@ -737,14 +748,9 @@ tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* 
 // ===========================================================================
 extern "C" {
 
-const char* tp_last_error(void) { return g_err.c_str(); }
-
-int tp_total_bins(const tp_scene* s) { return s ? s->total_bins : 0; }
-
-tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
-  g_err.clear();
-  if (!d || !out) return fail(TP_ERR_INVALID_ARG, "null argument");
-  *out = nullptr;
+// Checks a scene description and copies it into the host side of *s (no
+// device work).  Shared by tp_create_scene and the allocation-free call.
+static tp_status describe(const tp_scene_desc* d, tp_scene* s) {
   if (d->precision != TP_FP32 && d->precision != TP_FP64) return fail(TP_ERR_INVALID_ARG, "precision %d", d->precision);
   if (d->world_shape != TP_BOX && d->world_shape != TP_SPHERE) return fail(TP_ERR_INVALID_ARG, "world shape %d", d->world_shape);
   if (!finite_all(d->world_centre, 3) || !finite_all(d->world_params, 3)) return fail(TP_ERR_INVALID_ARG, "world not finite");
@@ -753,6 +759,7 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
   if (d->world_shape == TP_SPHERE && !(d->world_params[1] > 0)) return fail(TP_ERR_INVALID_ARG, "world radius must be positive");
   if (d->n_prims < 0 || (d->n_prims > 0 && !d->prims)) return fail(TP_ERR_INVALID_ARG, "prims");
   if (d->n_mirrors < 0 || (d->n_mirrors > 0 && !d->mirrors)) return fail(TP_ERR_INVALID_ARG, "mirrors");
+  if (d->n_choppers < 0 || (d->n_choppers > 0 && !d->choppers)) return fail(TP_ERR_INVALID_ARG, "choppers");
   if (d->n_tallies < 0 || d->n_tallies > TP_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))
     return fail(TP_ERR_INVALID_ARG, "n_tallies %d (max %d)", d->n_tallies, TP_MAX_TALLIES);
   if (d->n_instances < 1) return fail(TP_ERR_INVALID_ARG, "n_instances must be >= 1");
@@ -760,14 +767,13 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
   if (d->n_params > 0 && (!d->inst_params || !d->param_kind)) return fail(TP_ERR_INVALID_ARG, "inst_params / param_kind");
   if (d->event_cap < 0) return fail(TP_ERR_INVALID_ARG, "event_cap");
 
-  tp_scene* s = new tp_scene();
-  auto bail = [&](tp_status st) { tp_destroy_scene(s); return st; };
   s->precision = d->precision;
   s->event_cap = d->event_cap > 0 ? d->event_cap : 4096;
   s->world_shape = d->world_shape;
   for (int i = 0; i < 3; ++i) { s->world_c[i] = d->world_centre[i]; s->world_p[i] = d->world_params[i]; }
   s->prims.assign(d->prims, d->prims + d->n_prims);
   s->mirrors.assign(d->mirrors, d->mirrors + d->n_mirrors);
+  s->choppers.assign(d->choppers, d->choppers + d->n_choppers);
   s->source = d->source;
   s->tallies.assign(d->tallies, d->tallies + d->n_tallies);
   s->n_inst = d->n_instances;
@@ -777,41 +783,53 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
   s->inst_params.assign((size_t)s->n_inst * kMaxPar, 0.0);
   int n_radius = 0;
   for (int p = 0; p < s->n_par; ++p) {
-    if (s->param_kind[p] < TP_PAR_RADIUS || s->param_kind[p] > TP_PAR_DENSITY) return bail(fail(TP_ERR_INVALID_ARG, "param_kind[%d]", p));
+    if (s->param_kind[p] < TP_PAR_RADIUS || s->param_kind[p] > TP_PAR_DENSITY) return (fail(TP_ERR_INVALID_ARG, "param_kind[%d]", p));
     n_radius += s->param_kind[p] == TP_PAR_RADIUS;
   }
-  if (n_radius > 1) return bail(fail(TP_ERR_INVALID_ARG, "at most one radius parameter"));
+  if (n_radius > 1) return (fail(TP_ERR_INVALID_ARG, "at most one radius parameter"));
   for (int q = 0; q < s->n_inst; ++q)
     for (int p = 0; p < s->n_par; ++p) {
       const double v = d->inst_params[(size_t)q * s->n_par + p];
-      if (!std::isfinite(v)) return bail(fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] not finite", q, p));
-      if (s->param_kind[p] != TP_PAR_RADIUS && !(v > 0)) return bail(fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] must be > 0", q, p));
+      if (!std::isfinite(v)) return (fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] not finite", q, p));
+      if (s->param_kind[p] != TP_PAR_RADIUS && !(v > 0)) return (fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d] must be > 0", q, p));
       s->inst_params[(size_t)q * kMaxPar + p] = v;
     }
   // primitives
   for (int i = 0; i < d->n_prims; ++i) {
     const tp_prim& p = s->prims[i];
-    if (p.shape < TP_BOX || p.shape > TP_SPHERE) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: shape %d", i, p.shape));
-    if (p.axis < 0 || p.axis > 2) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: axis %d", i, p.axis));
-    if (p.role < TP_ROLE_BULK || p.role > TP_ROLE_BLACK) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: role %d", i, p.role));
-    if (p.mirror < -1 || p.mirror >= d->n_mirrors) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: mirror %d", i, p.mirror));
-    if (p.material < -1) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: material %d", i, p.material));
-    if (!finite_all(p.centre, 3) || !finite_all(p.params, 3)) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: not finite", i));
+    if (p.shape < TP_BOX || p.shape > TP_SPHERE) return (fail(TP_ERR_INVALID_ARG, "prim %d: shape %d", i, p.shape));
+    if (p.axis < 0 || p.axis > 2) return (fail(TP_ERR_INVALID_ARG, "prim %d: axis %d", i, p.axis));
+    if (p.role < TP_ROLE_BULK || p.role > TP_ROLE_BLACK) return (fail(TP_ERR_INVALID_ARG, "prim %d: role %d", i, p.role));
+    if (p.mirror < -1 || p.mirror >= d->n_mirrors) return (fail(TP_ERR_INVALID_ARG, "prim %d: mirror %d", i, p.mirror));
+    if (p.material < -1) return (fail(TP_ERR_INVALID_ARG, "prim %d: material %d", i, p.material));
+    if (!finite_all(p.centre, 3) || !finite_all(p.params, 3)) return (fail(TP_ERR_INVALID_ARG, "prim %d: not finite", i));
     if (p.shape == TP_BOX && !(p.params[0] > 0 && p.params[1] > 0 && p.params[2] > 0))
-      return bail(fail(TP_ERR_INVALID_ARG, "prim %d: box half extents must be positive", i));
-    if (p.shape == TP_TUBE && !(p.params[2] > 0)) return bail(fail(TP_ERR_INVALID_ARG, "prim %d: tube half height", i));
+      return (fail(TP_ERR_INVALID_ARG, "prim %d: box half extents must be positive", i));
+    if (p.shape == TP_TUBE && !(p.params[2] > 0)) return (fail(TP_ERR_INVALID_ARG, "prim %d: tube half height", i));
     if ((p.bind_rmin || p.bind_rmax) && (p.shape == TP_BOX || n_radius == 0))
-      return bail(fail(TP_ERR_INVALID_ARG, "prim %d: radius binding needs a tube/sphere and a radius parameter", i));
+      return (fail(TP_ERR_INVALID_ARG, "prim %d: radius binding needs a tube/sphere and a radius parameter", i));
+    if (p.chopper < -1 || p.chopper >= d->n_choppers) return (fail(TP_ERR_INVALID_ARG, "prim %d: chopper %d", i, p.chopper));
+    if (p.chopper >= 0 && (p.shape != TP_TUBE || p.material != -1 || p.role != TP_ROLE_BULK || p.mirror != -1 ||
+                           p.bind_rmin || p.bind_rmax))
+      return (fail(TP_ERR_INVALID_ARG, "prim %d: a chopper is a vacuum bulk tube, no mirror, no radius binding", i));
+  }
+  for (int i = 0; i < d->n_choppers; ++i) {
+    const tp_chopper& c = s->choppers[i];
+    if (!(c.r_black >= 0) || c.n_windows < 1 || c.n_windows > (1 << 20) || !(c.theta0 > 0) ||
+        !(c.theta0 <= 2.0 * M_PI) || !finite_all(&c.r_black, 1) || !finite_all(&c.freq, 1) ||
+        !finite_all(&c.phase, 1))
+      return (fail(TP_ERR_INVALID_ARG, "chopper %d: need r_black >= 0, n_windows >= 1, theta0 in (0, 2 pi], "
+                                       "finite freq and phase", i));
   }
   for (int i = 0; i < d->n_mirrors; ++i) {
     const tp_mirror& m = s->mirrors[i];
     if (!(m.R0 >= 0 && m.Qc >= 0 && m.W > 0 && m.alpha >= 0 && m.m >= 0) ||
         !finite_all(&m.m, 1) || !finite_all(&m.R0, 1))
-      return bail(fail(TP_ERR_INVALID_ARG, "mirror %d: need R0, Qc, alpha, m >= 0 and W > 0", i));
+      return (fail(TP_ERR_INVALID_ARG, "mirror %d: need R0, Qc, alpha, m >= 0 and W > 0", i));
   }
   // source
   if (!source_ok(s->source))
-    return bail(fail(TP_ERR_INVALID_ARG, "source: kind, wavelength range (> 0, lo <= hi) or temperature (>= 0), "
+    return (fail(TP_ERR_INVALID_ARG, "source: kind, wavelength range (> 0, lo <= hi) or temperature (>= 0), "
                                          "divergence in [0, 1.5) rad (none with a temperature unless "
                                          "TP_SRC_MODERATOR), slit beyond the moderator"));
   // tallies
@@ -819,25 +837,39 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
   long long tb = 0;
   for (int t = 0; t < d->n_tallies; ++t) {
     const tp_tally_desc& T = s->tallies[t];
-    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_DQ) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: kind", t));
-    if (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: trigger", t));
-    if (T.volume < -1 || T.volume >= d->n_prims) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: volume %d", t, T.volume));
-    if (T.volume == -1 && T.trigger == TP_PTS_ENTRY) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: the world has no ENTRY", t));
-    if (T.nbins[0] < 1 || T.nbins[1] < 1) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: bins", t));
-    if (T.kind == TP_TALLY_COUNT && (T.nbins[0] != 1 || T.nbins[1] != 1)) return bail(fail(TP_ERR_INVALID_ARG, "tally %d: a count has one bin", t));
-    if ((T.kind == TP_TALLY_ANGULAR || T.kind == TP_TALLY_MULTISCAT || T.kind == TP_TALLY_DQ) && T.nbins[1] != 1)
-      return bail(fail(TP_ERR_INVALID_ARG, "tally %d: a 1-D scorer has nbins[1] = 1", t));
+    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_TOF) return (fail(TP_ERR_INVALID_ARG, "tally %d: kind", t));
+    if (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) return (fail(TP_ERR_INVALID_ARG, "tally %d: trigger", t));
+    if (T.volume < -1 || T.volume >= d->n_prims) return (fail(TP_ERR_INVALID_ARG, "tally %d: volume %d", t, T.volume));
+    if (T.volume == -1 && T.trigger == TP_PTS_ENTRY) return (fail(TP_ERR_INVALID_ARG, "tally %d: the world has no ENTRY", t));
+    if (T.nbins[0] < 1 || T.nbins[1] < 1) return (fail(TP_ERR_INVALID_ARG, "tally %d: bins", t));
+    if (T.kind == TP_TALLY_COUNT && (T.nbins[0] != 1 || T.nbins[1] != 1)) return (fail(TP_ERR_INVALID_ARG, "tally %d: a count has one bin", t));
+    if ((T.kind == TP_TALLY_ANGULAR || T.kind == TP_TALLY_MULTISCAT || T.kind == TP_TALLY_DQ ||
+         T.kind == TP_TALLY_TOF) && T.nbins[1] != 1)
+      return (fail(TP_ERR_INVALID_ARG, "tally %d: a 1-D scorer has nbins[1] = 1", t));
     const int dims = (T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) ? 2 : (T.kind == TP_TALLY_COUNT ? 0 : 1);
     for (int k = 0; k < dims; ++k)
       if (!(T.hi[k] > T.lo[k]) || !std::isfinite(T.hi[k]) || !std::isfinite(T.lo[k]))
-        return bail(fail(TP_ERR_INVALID_ARG, "tally %d: range of axis %d", t, k));
+        return (fail(TP_ERR_INVALID_ARG, "tally %d: range of axis %d", t, k));
     s->tally_off[t] = (int)tb;
     tb += (long long)T.nbins[0] * T.nbins[1];
   }
-  if (tb > (1ll << 30)) return bail(fail(TP_ERR_INVALID_ARG, "too many bins"));
+  if (tb > (1ll << 30)) return (fail(TP_ERR_INVALID_ARG, "too many bins"));
   s->total_bins = (int)tb;
   s->tally_off[s->tallies.size()] = (int)tb;
-  tp_status st = validate_geometry(s);
+  return validate_geometry(s);
+}
+
+const char* tp_last_error(void) { return g_err.c_str(); }
+
+int tp_total_bins(const tp_scene* s) { return s ? s->total_bins : 0; }
+
+tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
+  g_err.clear();
+  if (!d || !out) return fail(TP_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tp_scene* s = new tp_scene();
+  auto bail = [&](tp_status st) { tp_destroy_scene(s); return st; };
+  tp_status st = describe(d, s);
   if (st != TP_OK) return bail(st);
   // device
   cudaError_t e = cudaGetDevice(&s->device);
@@ -1195,74 +1227,9 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   if (d->n_instances < 1 || d->n_instances > TP_NOALLOC_MAX_INSTANCES)
     return fail(TP_ERR_INVALID_ARG, "n_instances %d: the allocation-free call takes 1..%d", d->n_instances,
                 TP_NOALLOC_MAX_INSTANCES);
-  if (d->precision != TP_FP32 && d->precision != TP_FP64) return fail(TP_ERR_INVALID_ARG, "precision %d", d->precision);
-  if (d->world_shape != TP_BOX && d->world_shape != TP_SPHERE) return fail(TP_ERR_INVALID_ARG, "world shape %d", d->world_shape);
-  if (!finite_all(d->world_centre, 3) || !finite_all(d->world_params, 3)) return fail(TP_ERR_INVALID_ARG, "world not finite");
-  if (d->world_shape == TP_BOX && !(d->world_params[0] > 0 && d->world_params[1] > 0 && d->world_params[2] > 0))
-    return fail(TP_ERR_INVALID_ARG, "world half extents must be positive");
-  if (d->world_shape == TP_SPHERE && !(d->world_params[1] > 0)) return fail(TP_ERR_INVALID_ARG, "world radius must be positive");
-  if (d->n_prims < 0 || (d->n_prims > 0 && !d->prims) || d->n_mirrors < 0 || (d->n_mirrors > 0 && !d->mirrors))
-    return fail(TP_ERR_INVALID_ARG, "prims / mirrors");
-  if (d->n_tallies < 0 || d->n_tallies > TP_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))
-    return fail(TP_ERR_INVALID_ARG, "n_tallies %d (max %d)", d->n_tallies, TP_MAX_TALLIES);
-  if (d->n_params < 0 || d->n_params > TP_MAX_PARAMS || (d->n_params > 0 && (!d->inst_params || !d->param_kind)))
-    return fail(TP_ERR_INVALID_ARG, "parameters");
-  if (d->event_cap < 0) return fail(TP_ERR_INVALID_ARG, "event_cap");
-
   // host-side scene: the same checks and tables as tp_create_scene, no device memory
   tp_scene s;
-  s.precision = d->precision;
-  s.event_cap = d->event_cap > 0 ? d->event_cap : 4096;
-  s.world_shape = d->world_shape;
-  for (int i = 0; i < 3; ++i) { s.world_c[i] = d->world_centre[i]; s.world_p[i] = d->world_params[i]; }
-  s.prims.assign(d->prims, d->prims + d->n_prims);
-  s.mirrors.assign(d->mirrors, d->mirrors + d->n_mirrors);
-  s.source = d->source;
-  s.tallies.assign(d->tallies, d->tallies + d->n_tallies);
-  s.n_inst = d->n_instances;
-  s.n_par = d->n_params;
-  s.param_kind.assign(d->param_kind, d->param_kind + d->n_params);
-  s.radius_nominal = d->radius_nominal;
-  s.inst_params.assign((size_t)s.n_inst * kMaxPar, 0.0);
-  for (int q = 0; q < s.n_inst; ++q)
-    for (int p = 0; p < s.n_par; ++p) {
-      if (s.param_kind[p] < TP_PAR_RADIUS || s.param_kind[p] > TP_PAR_DENSITY) return fail(TP_ERR_INVALID_ARG, "param_kind[%d]", p);
-      const double v = d->inst_params[(size_t)q * s.n_par + p];
-      if (!std::isfinite(v) || (s.param_kind[p] != TP_PAR_RADIUS && !(v > 0)))
-        return fail(TP_ERR_INVALID_ARG, "inst_params[%d][%d]", q, p);
-      s.inst_params[(size_t)q * kMaxPar + p] = v;
-    }
-  for (int i = 0; i < d->n_prims; ++i) {
-    const tp_prim& p = s.prims[i];
-    if (p.shape < TP_BOX || p.shape > TP_SPHERE || p.axis < 0 || p.axis > 2 || p.role < TP_ROLE_BULK ||
-        p.role > TP_ROLE_BLACK || p.mirror < -1 || p.mirror >= d->n_mirrors || p.material < -1 ||
-        !finite_all(p.centre, 3) || !finite_all(p.params, 3))
-      return fail(TP_ERR_INVALID_ARG, "prim %d", i);
-    if (p.shape == TP_BOX && !(p.params[0] > 0 && p.params[1] > 0 && p.params[2] > 0))
-      return fail(TP_ERR_INVALID_ARG, "prim %d: box half extents must be positive", i);
-    if (p.shape == TP_TUBE && !(p.params[2] > 0)) return fail(TP_ERR_INVALID_ARG, "prim %d: tube half height", i);
-  }
-  for (int i = 0; i < d->n_mirrors; ++i) {
-    const tp_mirror& m = s.mirrors[i];
-    if (!(m.R0 >= 0 && m.Qc >= 0 && m.W > 0 && m.alpha >= 0 && m.m >= 0)) return fail(TP_ERR_INVALID_ARG, "mirror %d", i);
-  }
-  if (!source_ok(s.source)) return fail(TP_ERR_INVALID_ARG, "source");
-  s.tally_off.resize(s.tallies.size() + 1);
-  long long tb = 0;
-  for (int t = 0; t < d->n_tallies; ++t) {
-    const tp_tally_desc& T = s.tallies[t];
-    if (T.kind < TP_TALLY_COUNT || T.kind > TP_TALLY_DQ || (T.trigger != TP_PTS_ENTRY && T.trigger != TP_PTS_EXIT) ||
-        T.volume < -1 || T.volume >= d->n_prims || (T.volume == -1 && T.trigger == TP_PTS_ENTRY) ||
-        T.nbins[0] < 1 || T.nbins[1] < 1 || (T.kind != TP_TALLY_COUNT && !(T.hi[0] > T.lo[0])) ||
-        ((T.kind == TP_TALLY_PSD || T.kind == TP_TALLY_WLX) && !(T.hi[1] > T.lo[1])))
-      return fail(TP_ERR_INVALID_ARG, "tally %d", t);
-    s.tally_off[t] = (int)tb;
-    tb += (long long)T.nbins[0] * T.nbins[1];
-  }
-  if (tb > (1ll << 30)) return fail(TP_ERR_INVALID_ARG, "too many bins");
-  s.total_bins = (int)tb;
-  s.tally_off[s.tallies.size()] = (int)tb;
-  tp_status st = validate_geometry(&s);
+  tp_status st = describe(d, &s);
   if (st != TP_OK) return st;
   st = tp_set_materials(&s, mats, n_mats);
   if (st != TP_OK) return st;

@@ -17,8 +17,10 @@ enum { C_HIST = 0, C_EVENTS, C_COLL, C_CROSS, C_TRUNC, C_LOST, C_MIRROR, C_SEC }
 // History end codes (tp_record.end).
 enum { END_ESCAPED = 0, END_ABSORBED, END_DETECTED, END_BLACK, END_MIRROR, END_TRUNCATED,
        END_APERTURE, END_LOST };
-// Primitive flag bits.
-enum { F_BIND_RMIN = 1, F_BIND_RMAX = 2 };
+// Primitive flag bits; a chopper primitive also keeps its chopper index in
+// flags >> kChopperShift.
+enum { F_BIND_RMIN = 1, F_BIND_RMAX = 2, F_CHOPPER = 4 };
+constexpr int kChopperShift = 8;
 
 // One primitive as the kernels see it.  Lengths in the transport precision R.
 // entry_mask / exit_mask: bit t set if tally t listens to ENTRY / EXIT here.
@@ -50,6 +52,19 @@ struct alignas(16) DMirror {
   R m, R0, Qc, alpha, W, mQc, pad0, pad1;
 };
 
+// Disk chopper, in units of the window period: a neutron at angle phi (rad)
+// and time t (s) is at psi = phi * n_over_2pi - nf * t - n_phase periods from
+// window centres (integers) and passes if |psi - rint(psi)| <= half.
+template <typename R>
+struct alignas(16) DChopper {
+  R r_black2;     // black inner radius squared
+  R n_over_2pi;   // n / (2 pi)
+  R nf;           // n * freq
+  R n_phase;      // n * phase / (2 pi)
+  R half;         // n * theta0 / (4 pi)
+  R pad0, pad1, pad2;
+};
+
 template <typename R>
 struct alignas(16) DTally {
   R lo[2], hi[2];
@@ -65,7 +80,7 @@ template <typename R>
 struct KParams {
   const uint8_t* blob;
   uint32_t blob_bytes;
-  uint32_t off_prims, off_mats, off_mirrors, off_tallies, off_line_d, off_line_cum, off_nb;
+  uint32_t off_prims, off_mats, off_mirrors, off_choppers, off_tallies, off_line_d, off_line_cum, off_nb;
   int stage_blob;  // 1: copy the blob into shared memory
   int nprim, nmat, ntally, npar;
   int param_kind[kMaxPar];

@@ -60,6 +60,9 @@ template <> struct Tr<double> {
 
 // h^2 / (2 m_n) in meV A^2: E = kH2over2mn / lambda^2
 constexpr double kH2over2mn = 81.80420;
+// h / m_n in cm/s per A of wavelength: speed v = kHoverMn / lambda, so a path
+// of L cm takes L lambda / kHoverMn seconds
+constexpr double kHoverMn = 395603.4012;
 
 __device__ __forceinline__ float d_log(float x) { return logf(x); }
 __device__ __forceinline__ double d_log(double x) { return log(x); }
@@ -99,9 +102,9 @@ struct Particle {
   R x[3], u[3];
   R lam, w;
   R A[kMaxPar];
+  R s;       // path length flown since the source (time of flight s lam / kHoverMn)
   int vol, nscat;
-  uint32_t k, hid, inst, sub0, nsec;
-  int secondary;
+  uint32_t k, hid, inst, sub0, nsec;  // sub0 != 0: a radius-derivative secondary
   int last;  // primitive just left, flags and stuck count (see kNoPrim)
 };
 
@@ -110,6 +113,7 @@ struct View {
   const DPrim<R>* prims;
   const DMat<R>* mats;
   const DMirror<R>* mirrors;
+  const DChopper<R>* choppers;
   const DTally<R>* tallies;
   const R* line_d;
   const R* line_cum;
@@ -515,9 +519,10 @@ __device__ __forceinline__ R tally_angle(const DTally<R>& T, R x0, R x1, R x2) {
 }
 
 template <typename R>
-__device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam, int nscat) {
+__device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam, int nscat, R path) {
   switch (T.kind) {
     case TP_TALLY_COUNT: return 0;
+    case TP_TALLY_TOF: return bin1(path * lam * R(1.0 / kHoverMn), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
     case TP_TALLY_ANGULAR: return bin1(tally_angle(T, x0, x1, x2), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
     case TP_TALLY_MULTISCAT: return bin1((R)nscat, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
     case TP_TALLY_DQ: {
@@ -545,7 +550,7 @@ __device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R
 template <typename R, bool GRAD>
 __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>* tallies, unsigned mask, int face,
                                        R x0, R x1, R x2, R lam, R w_, R A0, R A1, R A2, R A3, int nscat,
-                                       uint32_t inst, int secondary) {
+                                       uint32_t inst, bool secondary, R path) {
   const R A[kMaxPar] = {A0, A1, A2, A3};
   while (mask) {
     const int t = __ffs(mask) - 1;
@@ -553,7 +558,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     const DTally<R>& T = tallies[t];
     if (T.face >= 0 && T.face != face) continue;
     if (T.scat >= 0 && T.scat != nscat) continue;
-    const int b = tally_bin(T, x0, x1, x2, lam, nscat);
+    const int b = tally_bin(T, x0, x1, x2, lam, nscat, path);
     if (b < 0) continue;
     const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
     const double w = (double)w_;
@@ -578,7 +583,7 @@ template <typename R, bool GRAD>
 __device__ __forceinline__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>& P, unsigned mask,
                                       int face) {
   score_out<R, GRAD>(kp, V.tallies, mask, face, P.x[0], P.x[1], P.x[2], P.lam, P.w, P.A[0], P.A[1], P.A[2],
-                     P.A[3], P.nscat, P.inst, P.secondary);
+                     P.A[3], P.nscat, P.inst, P.sub0 != 0u, P.s);
 }
 
 // ---------------------------------------------------------------------------
@@ -625,7 +630,7 @@ __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R
   P.w = R(1);
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
-  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.secondary = 0; P.last = kNoPrim;
+  P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.s = R(0); P.last = kNoPrim;
   if (kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
                           fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
     P.w = R(0);
@@ -709,7 +714,6 @@ __device__ __forceinline__ bool radius_crossing(const KParams<R>& kp, const View
   const int mat = pick < 2 ? mi : mo;
   const int proc = (pick & 1) ? TP_PROC_BRAGG : TP_PROC_INC;
   *S = P;
-  S->secondary = 1;
   S->w = P.w * (tp > R(0) ? R(1) : R(-1)) * C / cosn;
   S->nscat = P.nscat + 1;
   S->sub0 = 4u + 2u * P.nsec;
@@ -735,6 +739,23 @@ __device__ __forceinline__ bool radius_crossing(const KParams<R>& kp, const View
 // lives, else its end code; advance returns kOutCross / kOutColl instead.
 // ---------------------------------------------------------------------------
 constexpr int kOutCross = 100, kOutColl = 101;
+
+// Disk chopper in ray-tracing mode (Eq. eRayTracing, §3.5): epsilon = 1 if the
+// neutron entering the disk's tube is outside the black centre and inside an
+// opening window at its time of flight, else 0.  Angles are counted in window
+// periods so that the comparison stays exact in FP32 over many turns.
+template <typename R>
+__device__ __forceinline__ bool chopper_open(const View<R>& V, const DPrim<R>& pt, const Particle<R>& P) {
+  const DChopper<R>& ch = V.choppers[pt.flags >> kChopperShift];
+  // in-plane axes (axis+1, axis+2) mod 3, as in the tube's local frame
+  const R d0 = P.x[0] - pt.c[0], d1 = P.x[1] - pt.c[1], d2 = P.x[2] - pt.c[2];
+  const R q1 = pt.axis == 0 ? d1 : (pt.axis == 1 ? d2 : d0);
+  const R q2 = pt.axis == 0 ? d2 : (pt.axis == 1 ? d0 : d1);
+  if (q1 * q1 + q2 * q2 < ch.r_black2) return false;
+  const R t = P.s * P.lam * R(1.0 / kHoverMn);
+  const R psi = d_atan2(q2, q1) * ch.n_over_2pi - ch.nf * t - ch.n_phase;
+  return fabs(psi - rint(psi)) <= ch.half;
+}
 
 // Entry test of primitive i from the world region, with the bounding-sphere
 // early-out and the rules for the primitive just left; keeps the nearest.
@@ -881,8 +902,9 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) P.x[i] += x * P.u[i];
+  P.s += x;
   if (sig_g != sig_t) P.w *= d_exp((sig_g - sig_t) * x);
-  if (GRAD && mat >= 0 && !P.secondary) {
+  if (GRAD && mat >= 0 && P.sub0 == 0u) {
     const DMat<R>& m = V.mats[mat];
 #pragma unroll
     for (int p = 0; p < kMaxPar; ++p) {
@@ -909,7 +931,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
     const int v = locate_after(kp, V, dR, xn, from);
     P.last = (P.last & kStuckMask) | from | (hull_face(pf.shape, face) ? kLastHull : 0);
-    if (GRAD && kp.radius_par >= 0 && !P.secondary && pf.shape != TP_BOX &&
+    if (GRAD && kp.radius_par >= 0 && P.sub0 == 0u && pf.shape != TP_BOX &&
         ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
       R n[3];
       normal(pf, P.x, face, n);
@@ -929,6 +951,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
       if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, -1);
       if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
       if (pt.role == TP_ROLE_BLACK) return END_BLACK;
+      if ((pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
     }
     return -1;
   }
@@ -955,7 +978,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
     return -1;
   }
-  if (GRAD && kp.radius_par >= 0 && !P.secondary && pt.shape != TP_BOX &&
+  if (GRAD && kp.radius_par >= 0 && P.sub0 == 0u && pt.shape != TP_BOX &&
       ((face == 0 && (pt.flags & F_BIND_RMAX)) || (face == 1 && (pt.flags & F_BIND_RMIN)))) {
     R n[3];
     normal(pt, P.x, face, n);
@@ -971,6 +994,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
   if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
   if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
   if (pt.role == TP_ROLE_BLACK) return END_BLACK;
+  if ((pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
   return -1;
 }
 
@@ -981,7 +1005,7 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
                        const uint4 r0, const R sig[TP_NPROC], R sig_g) {
   cnt[C_COLL]++;
   const int mat = V.prims[P.vol].material;
-  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+  if (kp.records && P.sub0 == 0u && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
     tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->first_collision[0] = (double)P.x[0];
     rc->first_collision[1] = (double)P.x[1];
@@ -996,7 +1020,7 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
   else if (m.g[2] * sig[2] > R(0)) j = 2;
   else j = (m.g[1] * sig[1] > R(0)) ? 1 : 0;
   P.w /= m.g[j];
-  if (GRAD && !P.secondary) {
+  if (GRAD && P.sub0 == 0u) {
 #pragma unroll
     for (int p = 0; p < kMaxPar; ++p) {
       if (p >= kp.npar) break;
@@ -1011,7 +1035,7 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
     xline = Tr<R>::u01(r1.x);
   }
   scatter_dir(V, mat, j, P.lam, P.u, Tr<R>::u01(r0.z), Tr<R>::u01(r0.w), xline);
-  if (kp.records && !P.secondary && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+  if (kp.records && P.sub0 == 0u && P.nscat == 0 && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
     tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->dir_after_first[0] = (double)P.u[0];
     rc->dir_after_first[1] = (double)P.u[1];
@@ -1088,7 +1112,7 @@ __device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, u
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& P, int end) {
-  if (kp.records && !P.secondary && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
+  if (kp.records && P.sub0 == 0u && P.inst == 0 && P.hid - kp.inst_first[0] < kp.n_records) {
     tp_record* rc = kp.records + (P.hid - kp.inst_first[0]);
     rc->final_pos[0] = (double)P.x[0];
     rc->final_pos[1] = (double)P.x[1];
@@ -1117,6 +1141,7 @@ __global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KP
   V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
   V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
   V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.choppers = reinterpret_cast<const DChopper<R>*>(base + kp.off_choppers);
   V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
   V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
   V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
@@ -1255,6 +1280,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__
   V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
   V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
   V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.choppers = reinterpret_cast<const DChopper<R>*>(base + kp.off_choppers);
   V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
   V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
   V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
@@ -1444,6 +1470,7 @@ __global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__
   V.prims = reinterpret_cast<const DPrim<R>*>(base + kp.off_prims);
   V.mats = reinterpret_cast<const DMat<R>*>(base + kp.off_mats);
   V.mirrors = reinterpret_cast<const DMirror<R>*>(base + kp.off_mirrors);
+  V.choppers = reinterpret_cast<const DChopper<R>*>(base + kp.off_choppers);
   V.tallies = reinterpret_cast<const DTally<R>*>(base + kp.off_tallies);
   V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
   V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);

@@ -17,7 +17,8 @@ from . import native as N
 _SHAPES = {"box": N.TP_BOX, "tube": N.TP_TUBE, "sphere": N.TP_SPHERE}
 _ROLES = {"bulk": N.TP_ROLE_BULK, "detector": N.TP_ROLE_DETECTOR, "black": N.TP_ROLE_BLACK}
 _TALLY = {"count": N.TP_TALLY_COUNT, "angular": N.TP_TALLY_ANGULAR, "psd": N.TP_TALLY_PSD,
-          "wlx": N.TP_TALLY_WLX, "multiscat": N.TP_TALLY_MULTISCAT, "dq": N.TP_TALLY_DQ}
+          "wlx": N.TP_TALLY_WLX, "multiscat": N.TP_TALLY_MULTISCAT, "dq": N.TP_TALLY_DQ,
+          "tof": N.TP_TALLY_TOF}
 _PTS = {"entry": N.TP_PTS_ENTRY, "exit": N.TP_PTS_EXIT}
 _PAR = {"radius": N.TP_PAR_RADIUS, "scale": N.TP_PAR_SCALE, "density": N.TP_PAR_DENSITY}
 
@@ -33,6 +34,73 @@ def source_struct(src: dict) -> N.tp_source:
                        N.D2(*src.get("slit_half", (0.0, 0.0))), float(src.get("temperature", 0.0)))
 
 
+def scene_struct(desc: dict, precision: str | None = None):
+    """The workload description as a tp_scene_desc; returns (desc struct,
+    objects to keep alive while it is used)."""
+    prims = desc["prims"]
+    mirrors, choppers = [], []
+    P = (N.tp_prim * max(1, len(prims)))()
+    for i, p in enumerate(prims):
+        mi = ci = -1
+        if p.get("mirror"):
+            mi = len(mirrors)
+            mirrors.append(p["mirror"])
+        if p.get("chopper"):
+            ci = len(choppers)
+            choppers.append(p["chopper"])
+        P[i] = N.tp_prim(shape=_SHAPES[p["shape"]], axis=p["axis"], material=p["material"],
+                         role=_ROLES[p["role"]], mirror=mi, bind_rmin=int(p["bind_rmin"]),
+                         bind_rmax=int(p["bind_rmax"]), chopper=ci, centre=N.D3(*p["centre"]),
+                         params=N.D3(*p["params"]))
+    M = (N.tp_mirror * max(1, len(mirrors)))()
+    for i, m in enumerate(mirrors):
+        M[i] = N.tp_mirror(m["m"], m["R0"], m["Qc"], m["alpha"], m["W"])
+    CH = (N.tp_chopper * max(1, len(choppers)))()
+    for i, c in enumerate(choppers):
+        CH[i] = N.tp_chopper(c["r_black"], c["n"], c["freq"], c["theta0"], c["phase"])
+    tallies = desc["tallies"]
+    T = (N.tp_tally_desc * max(1, len(tallies)))()
+    for i, t in enumerate(tallies):
+        T[i] = N.tp_tally_desc(_TALLY[t["kind"]], _PTS[t["trigger"]], t["volume"], t["face"],
+                               t["scat"], N.I2(*t["bins"]), N.D2(*t["lo"]), N.D2(*t["hi"]),
+                               N.D3(*t["origin"]), N.D3(*t["axis"]))
+    inst = desc["instances"]
+    params = np.ascontiguousarray(inst["params"], dtype=np.float64)
+    n_par = len(desc["params"])
+    pk = np.array([_PAR[p["kind"]] for p in desc["params"]] or [0], dtype=np.int32)
+    pflat = np.ascontiguousarray(params.reshape(-1)) if n_par else np.zeros(1)
+    prec = precision or desc.get("precision", "f32")
+    w = desc["world"]
+    d = N.tp_scene_desc(world_shape=_SHAPES[w["shape"]], world_centre=N.D3(*w["centre"]),
+                        world_params=N.D3(*w["params"]), n_prims=len(prims), prims=P,
+                        n_mirrors=len(mirrors), mirrors=M, source=source_struct(desc["source"]),
+                        n_tallies=len(tallies), tallies=T, n_instances=int(params.shape[0]),
+                        inst_params=pflat.ctypes.data_as(N.DP), n_params=n_par,
+                        param_kind=pk.ctypes.data_as(C.POINTER(C.c_int)),
+                        radius_nominal=float(inst.get("radius_nominal", 0.0)),
+                        precision=N.TP_FP64 if prec == "f64" else N.TP_FP32,
+                        event_cap=int(desc.get("event_cap", 0)), n_choppers=len(choppers), choppers=CH)
+    return d, [P, M, CH, T, pk, pflat]
+
+
+def material_structs(mats):
+    """tp_material array for a list of material descriptions; returns (array,
+    objects to keep alive)."""
+    arr, keep = (N.tp_material * max(1, len(mats)))(), []
+    for i, m in enumerate(mats):
+        br = m.get("bragg")
+        if br:
+            a = [np.ascontiguousarray(br[k], dtype=np.float64) for k in ("d", "mult", "F2")]
+            keep += a
+            arr[i] = N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"), m["sigma_inc"], len(a[0]),
+                                   br["V0"], *[x.ctypes.data_as(N.DP) for x in a], m["density_param"],
+                                   m["scale_param"])
+        else:
+            arr[i] = N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"), m["sigma_inc"], 0, 1.0,
+                                   None, None, None, m["density_param"], m["scale_param"])
+    return arr, keep
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -46,41 +114,13 @@ class Scene:
         self.desc = desc
         self._keep = []
         prec = precision or desc.get("precision", "f32")
-        prims = desc["prims"]
-        mirrors = []
-        P = (N.tp_prim * max(1, len(prims)))()
-        for i, p in enumerate(prims):
-            mi = -1
-            if p.get("mirror"):
-                mi = len(mirrors)
-                mirrors.append(p["mirror"])
-            P[i] = N.tp_prim(_SHAPES[p["shape"]], p["axis"], p["material"], _ROLES[p["role"]], mi,
-                             int(p["bind_rmin"]), int(p["bind_rmax"]), N.D3(*p["centre"]),
-                             N.D3(*p["params"]))
-        M = (N.tp_mirror * max(1, len(mirrors)))()
-        for i, m in enumerate(mirrors):
-            M[i] = N.tp_mirror(m["m"], m["R0"], m["Qc"], m["alpha"], m["W"])
-        S = source_struct(desc["source"])
-        tallies = desc["tallies"]
-        T = (N.tp_tally_desc * max(1, len(tallies)))()
-        for i, t in enumerate(tallies):
-            T[i] = N.tp_tally_desc(_TALLY[t["kind"]], _PTS[t["trigger"]], t["volume"], t["face"],
-                                   t["scat"], N.I2(*t["bins"]), N.D2(*t["lo"]), N.D2(*t["hi"]),
-                                   N.D3(*t["origin"]), N.D3(*t["axis"]))
+        d, keep = scene_struct(desc, prec)
+        self._keep += keep
         inst = desc["instances"]
         params = np.ascontiguousarray(inst["params"], dtype=np.float64)
         self.n_inst = int(params.shape[0])
         self.n_par = len(desc["params"])
-        pk = np.array([_PAR[p["kind"]] for p in desc["params"]] or [0], dtype=np.int32)
-        pflat = np.ascontiguousarray(params.reshape(-1)) if self.n_par else np.zeros(1)
-        self._keep += [P, M, T, pk, pflat]
-        w = desc["world"]
-        d = N.tp_scene_desc(_SHAPES[w["shape"]], N.D3(*w["centre"]), N.D3(*w["params"]),
-                            len(prims), P, len(mirrors), M, S, len(tallies), T, self.n_inst,
-                            pflat.ctypes.data_as(N.DP), self.n_par,
-                            pk.ctypes.data_as(C.POINTER(C.c_int)),
-                            float(inst.get("radius_nominal", 0.0)),
-                            N.TP_FP64 if prec == "f64" else N.TP_FP32, int(desc.get("event_cap", 0)))
+        tallies = desc["tallies"]
         self.handle = N.tp_create_scene(d)
         self.precision = prec
         self.params = params.copy()
@@ -96,23 +136,9 @@ class Scene:
 
     # ------------------------------------------------------------------
     def set_materials(self, mats) -> None:
-        arr = []
-        for m in mats:
-            br = m.get("bragg")
-            if br:
-                d = np.ascontiguousarray(br["d"], dtype=np.float64)
-                mu = np.ascontiguousarray(br["mult"], dtype=np.float64)
-                f2 = np.ascontiguousarray(br["F2"], dtype=np.float64)
-                self._keep += [d, mu, f2]
-                arr.append(N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"),
-                                         m["sigma_inc"], len(d), br["V0"], d.ctypes.data_as(N.DP),
-                                         mu.ctypes.data_as(N.DP), f2.ctypes.data_as(N.DP),
-                                         m["density_param"], m["scale_param"]))
-            else:
-                arr.append(N.tp_material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"),
-                                         m["sigma_inc"], 0, 1.0, None, None, None,
-                                         m["density_param"], m["scale_param"]))
-        N.tp_set_materials(self.handle, arr)
+        arr, keep = material_structs(mats)
+        self._keep += keep
+        N.tp_set_materials(self.handle, list(arr)[: len(mats)])
 
     def set_bias(self, material: int, g) -> None:
         N.tp_set_bias(self.handle, material, g)

@@ -16,7 +16,7 @@ STATUS_NAMES = ["TP_OK", "TP_ERR_INVALID_ARG", "TP_ERR_GEOMETRY", "TP_ERR_CUDA",
 TP_BOX, TP_TUBE, TP_SPHERE = 0, 1, 2
 TP_ROLE_BULK, TP_ROLE_DETECTOR, TP_ROLE_BLACK = 0, 1, 2
 TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3
-TP_TALLY_COUNT, TP_TALLY_ANGULAR, TP_TALLY_PSD, TP_TALLY_WLX, TP_TALLY_MULTISCAT, TP_TALLY_DQ = 0, 1, 2, 3, 4, 5
+TP_TALLY_COUNT, TP_TALLY_ANGULAR, TP_TALLY_PSD, TP_TALLY_WLX, TP_TALLY_MULTISCAT, TP_TALLY_DQ, TP_TALLY_TOF = range(7)
 TP_PTS_ENTRY, TP_PTS_EXIT = 0, 1
 TP_PAR_RADIUS, TP_PAR_SCALE, TP_PAR_DENSITY = 0, 1, 2
 TP_SRC_PENCIL, TP_SRC_RECT, TP_SRC_MODERATOR = 0, 1, 2
@@ -35,13 +35,18 @@ I2 = C.c_int * 2
 
 class tp_prim(C.Structure):
     _fields_ = [("shape", C.c_int), ("axis", C.c_int), ("material", C.c_int), ("role", C.c_int),
-                ("mirror", C.c_int), ("bind_rmin", C.c_int), ("bind_rmax", C.c_int),
+                ("mirror", C.c_int), ("bind_rmin", C.c_int), ("bind_rmax", C.c_int), ("chopper", C.c_int),
                 ("centre", D3), ("params", D3)]
 
 
 class tp_mirror(C.Structure):
     _fields_ = [("m", C.c_double), ("R0", C.c_double), ("Qc", C.c_double), ("alpha", C.c_double),
                 ("W", C.c_double)]
+
+
+class tp_chopper(C.Structure):
+    _fields_ = [("r_black", C.c_double), ("n_windows", C.c_int), ("freq", C.c_double),
+                ("theta0", C.c_double), ("phase", C.c_double)]
 
 
 class tp_tally_desc(C.Structure):
@@ -65,7 +70,8 @@ class tp_scene_desc(C.Structure):
                 ("n_tallies", C.c_int), ("tallies", C.POINTER(tp_tally_desc)),
                 ("n_instances", C.c_int), ("inst_params", C.POINTER(C.c_double)),
                 ("n_params", C.c_int), ("param_kind", C.POINTER(C.c_int)),
-                ("radius_nominal", C.c_double), ("precision", C.c_int), ("event_cap", C.c_int)]
+                ("radius_nominal", C.c_double), ("precision", C.c_int), ("event_cap", C.c_int),
+                ("n_choppers", C.c_int), ("choppers", C.POINTER(tp_chopper))]
 
 
 class tp_material(C.Structure):

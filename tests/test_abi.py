@@ -35,8 +35,8 @@ def test_every_declared_symbol_is_exported(native):
 
 
 def test_struct_layout_matches_header(native, tmp_path):
-    structs = ["tp_prim", "tp_mirror", "tp_tally_desc", "tp_source", "tp_scene_desc", "tp_material",
-               "tp_record", "tp_run"]
+    structs = ["tp_prim", "tp_mirror", "tp_chopper", "tp_tally_desc", "tp_source", "tp_scene_desc",
+               "tp_material", "tp_record", "tp_run"]
     src = tmp_path / "sz.c"
     body = "".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     src.write_text(f'#include <stdio.h>\n#include "tp.h"\nint main(void){{{body}return 0;}}\n')
@@ -49,7 +49,7 @@ def test_struct_layout_matches_header(native, tmp_path):
 
 def _desc(native, **kw):
     N = native
-    prims = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, N.D3(0, 0, 0.5), N.D3(5, 5, 0.5)))
+    prims = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, -1, N.D3(0, 0, 0.5), N.D3(5, 5, 0.5)))
     src = N.tp_source(N.TP_SRC_PENCIL, N.D3(0, 0, -1), N.D2(0, 0), 1.8, 1.8, N.D2(0, 0), 0, N.D2(0, 0),
                       0.0, N.D2(0, 0), 0.0)
     tallies = (N.tp_tally_desc * 1)(N.tp_tally_desc(N.TP_TALLY_COUNT, N.TP_PTS_EXIT, 0, 5, -1, N.I2(1, 1),
@@ -78,14 +78,14 @@ def test_invalid_descriptions_rejected_before_device_work(native, field, value, 
 def test_invalid_primitives_rejected(native):
     N = native
     d = _desc(native)
-    bad = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, N.D3(0, 0, 0.5), N.D3(-1, 5, 0.5)))
+    bad = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, -1, N.D3(0, 0, 0.5), N.D3(-1, 5, 0.5)))
     d.prims = bad
     assert native.lib.tp_create_scene(C.byref(d), C.byref(C.c_void_p())) == N.TP_ERR_INVALID_ARG
-    outside = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, N.D3(0, 0, 99.0), N.D3(5, 5, 5)))
+    outside = (N.tp_prim * 1)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, -1, N.D3(0, 0, 99.0), N.D3(5, 5, 5)))
     d.prims = outside
     assert native.lib.tp_create_scene(C.byref(d), C.byref(C.c_void_p())) == N.TP_ERR_GEOMETRY
-    two = (N.tp_prim * 2)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, N.D3(0, 0, 0.5), N.D3(5, 5, 0.5)),
-                          N.tp_prim(N.TP_SPHERE, 2, 0, 0, -1, 0, 0, N.D3(1, 1, 0.8), N.D3(0, 1.0, 0)))
+    two = (N.tp_prim * 2)(N.tp_prim(N.TP_BOX, 2, 0, 0, -1, 0, 0, -1, N.D3(0, 0, 0.5), N.D3(5, 5, 0.5)),
+                          N.tp_prim(N.TP_SPHERE, 2, 0, 0, -1, 0, 0, -1, N.D3(1, 1, 0.8), N.D3(0, 1.0, 0)))
     d.prims = two
     d.n_prims = 2
     assert native.lib.tp_create_scene(C.byref(d), C.byref(C.c_void_p())) == N.TP_ERR_GEOMETRY
@@ -99,3 +99,39 @@ def test_null_arguments(native):
     assert N.lib.tp_set_materials(None, None, 0) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_read_tallies(None, 0, 0, None, None, 0) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_total_bins(None) == 0
+
+
+def test_invalid_choppers_rejected_before_device_work(native):
+    N = native
+    d = _desc(native)
+    tube = lambda **kw: N.tp_prim(**{"shape": N.TP_TUBE, "axis": 2, "material": -1, "role": 0, "mirror": -1,
+                                    "bind_rmin": 0, "bind_rmax": 0, "chopper": 0, "centre": N.D3(0, 0, 0.5),
+                                    "params": N.D3(0, 5, 0.05), **kw})
+    good = N.tp_chopper(1.0, 4, 100.0, 0.35, 0.0)
+    cases = [
+        (tube(shape=N.TP_BOX, params=N.D3(5, 5, 0.05)), good),   # not a tube
+        (tube(material=0), good),                                # not vacuum
+        (tube(chopper=1), good),                                 # index out of range
+        (tube(), N.tp_chopper(1.0, 0, 100.0, 0.35, 0.0)),        # no window
+        (tube(), N.tp_chopper(1.0, 4, 100.0, 0.0, 0.0)),         # closed window
+        (tube(), N.tp_chopper(-1.0, 4, 100.0, 0.35, 0.0)),       # negative radius
+        (tube(), N.tp_chopper(1.0, 4, float("nan"), 0.35, 0.0)),  # no frequency
+    ]
+    for prim, ch in cases:
+        prims = (N.tp_prim * 1)(prim)
+        chs = (N.tp_chopper * 1)(ch)
+        d.prims, d.n_choppers, d.choppers = prims, 1, chs
+        out = C.c_void_p()
+        assert N.lib.tp_create_scene(C.byref(d), C.byref(out)) == N.TP_ERR_INVALID_ARG, (prim.shape, ch.n_windows)
+        assert out.value is None
+        assert "chopper" in N.tp_last_error()
+
+
+def test_tof_scorer_is_one_dimensional(native):
+    N = native
+    d = _desc(native)
+    t = (N.tp_tally_desc * 1)(N.tp_tally_desc(N.TP_TALLY_TOF, N.TP_PTS_EXIT, 0, -1, -1, N.I2(10, 2),
+                                              N.D2(0, 0), N.D2(0.01, 1), N.D3(0, 0, 0), N.D3(0, 0, 1)))
+    d.tallies = t
+    assert N.lib.tp_create_scene(C.byref(d), C.byref(C.c_void_p())) == N.TP_ERR_INVALID_ARG
+    assert "1-D" in N.tp_last_error()

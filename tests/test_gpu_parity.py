@@ -444,3 +444,62 @@ def test_moderator_guns_fp32_statistics(eng, orc, T):
     m2, e2 = stats(o["sum"], o["sumsq"], n // 4)
     ok, info = compare_tallies(m1, e1, m2, e2)
     assert ok, info
+
+
+# ---------------------------------------------------------------------------
+# Disk chopper (ray-tracing mode) and time-of-flight scorers
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_chopper_fp64_matches_oracle_history_by_history(eng, orc, kernel):
+    n = 20_000
+    for desc in (W.chopper(n_histories=n, precision="f64"),
+                 W.chopper_pencil(n_histories=n, phase_deg=-40.0, disk_centre=(12.0, 9.0)),
+                 W.chopper_pencil(n_histories=n, temperature=293.0, disk_centre=(0.0, -12.0))):
+        gpu = gpu_run(eng, desc, n, records=n, kernel=kernel)
+        o = orc.OracleScene(desc).run(n, records=True)
+        assert np.allclose(gpu["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12), desc["name"]
+        assert (gpu["records"]["end"] == o["records"]["end"]).all(), desc["name"]
+        assert np.allclose(gpu["records"]["final_pos"], o["records"]["final_pos"], rtol=1e-9, atol=1e-9)
+
+
+def test_chopper_fp32_statistics_and_transmission(eng, orc):
+    n = 4_000_000
+    desc = W.chopper(n_histories=n)
+    raw = gpu_run(eng, desc, n)["raw"]
+    m1, e1 = stats(raw["sum"], raw["sumsq"], n)
+    o = orc.OracleScene(desc).run(n // 4)
+    m2, e2 = stats(o["sum"], o["sumsq"], n // 4)
+    ok, info = compare_tallies(m1, e1, m2, e2)
+    assert ok, info
+    # pencil beam: transmitted fraction from the open intervals in time
+    from test_oracle_chopper import open_measure, flight_path, H_OVER_MN
+    desc = W.chopper_pencil(n_histories=n, precision="f32")
+    raw = gpu_run(eng, desc, n)["raw"]
+    L = flight_path(desc)
+    t1, t2 = (L * lam / H_OVER_MN for lam in desc["source"]["lambda"])
+    p = open_measure(t1, t2, desc) / (t2 - t1)
+    assert abs(raw["sum"][-1] / n - p) <= 4.5 * math.sqrt(p * (1 - p) / n), (raw["sum"][-1] / n, p)
+
+
+def test_chopper_study_peaks_on_gpu_at_full_statistics(eng):
+    import json
+    from pathlib import Path
+    g = json.loads((Path(__file__).parent / "golden" / "chopper_study.json").read_text())
+    n = 50_000_000
+    desc = W.chopper(n_histories=n)
+    raw = gpu_run(eng, desc, n)["raw"]
+    after = raw["sum"][1000:2000]
+    dt = 0.025 / 1000
+    # peak support midpoints: runs of non-empty bins
+    nz = np.nonzero(after)[0]
+    runs, start = [], nz[0]
+    for a, b in zip(nz[:-1], nz[1:]):
+        if b - a > 1:
+            runs.append((start, a))
+            start = b
+    runs.append((start, nz[-1]))
+    mids = [(lo + hi + 1) * 0.5 * dt for lo, hi in runs if after[lo:hi + 1].sum() >= 1000]
+    sp = g["peak_spacing_s"]
+    in_range = [t for t in mids if 0.8 * sp <= t <= 1.05 * g["printed"]["n_peaks"] * sp]
+    assert len(in_range) == g["printed"]["n_peaks"], mids
+    assert np.all(np.abs(np.diff(in_range) - sp) < 2 * dt), np.diff(in_range)

@@ -373,7 +373,7 @@ def chopper(n_histories: int = 10_000_000, precision: str = "f32", tof_bins: int
     at radius 19 cm, at 90 degrees from the first in-plane axis, so that a
     window is centred on the beam at t = 0.  Time-of-flight scorers on the
     chopper's ENTRY (just before it) and EXIT (just after it), 25 us bins."""
-    world = {"shape": BOX, "centre": (0.0, 0.0, -495.0), "params": (40.0, 40.0, 510.0)}
+    world = {"shape": BOX, "centre": (0.0, 0.0, -495.0), "params": (50.0, 50.0, 510.0)}
     src = moderator_source(src_w=0.1, src_h=0.1, src_z=-CHOPPER_DISTANCE, slit_w=4.5, slit_h=4.5,
                            slit_z=0.0, temperature=293.0)
     disk = disk_chopper(r_black=13.0, n=4, freq=100.0, theta0_deg=20.0, phase_deg=0.0)
