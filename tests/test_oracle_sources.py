@@ -92,9 +92,15 @@ def test_uniform_gun_hits_the_slit_uniformly(orc):
 
 
 def test_uniform_gun_spectrum_is_flat_on_its_interval(orc):
+    import json
+    from pathlib import Path
+    g = json.loads((Path(__file__).parent / "golden" / "uni_moderator_gun.json").read_text())
+    src = W.moderator_source(mean_wl=g["parameters"]["mean_wl"], range_wl=g["parameters"]["range_wl"])
+    assert math.isclose(src["lambda"][0], g["printed"]["lambda_min"])
+    assert math.isclose(src["lambda"][1], g["printed"]["lambda_max"])
     desc, psd, spec = run(orc)
     lo, hi = desc["source"]["lambda"]
-    assert math.isclose(lo, 3.09) and math.isclose(hi, 3.69)
+    assert (lo, hi) == src["lambda"]
     edges = np.linspace(0.2, 8.2, 61)
     chi2_check(spec, bin_probs(uniform_cdf(lo, hi), edges))
 
