@@ -159,8 +159,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     n = int(desc["instances"]["counts"].sum())
     sc = Scene(desc)
     bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
-    runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, graph=True,
-                                   first=first)) if grad else None
+    runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
+                                   graph=True, first=first)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     first = rank * n   # disjoint history ids per rank: weak scaling
@@ -170,7 +170,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             runs(st)
             sc.backward(bgrad, stream=st)
         else:
-            sc.run(n, first=first, stream=st, kernel=args.kernel)
+            sc.run(n, first=first, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
 
     # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
     for _ in range(args.warmup):
@@ -228,7 +228,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             g = sc.backward(bgrad)
             host_grad[:, : sc.n_par] = g.cpu().numpy()
         else:
-            sc.run(n, first=first, kernel=args.kernel)
+            sc.run(n, first=first, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
         for t in range(len(sc.tally_bins)):
             o = sc.tally_off[t]
             NN.tp_read_tallies(sc.handle, t, q, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
@@ -397,7 +397,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powder")
     ap.add_argument("--histories", type=int, default=0, help="override the histories per step")
-    ap.add_argument("--kernel", type=int, default=0, help="0 autotuned, 1 history-based, 2 event-based")
+    ap.add_argument("--kernel", type=int, default=0, help="0 autotuned, 1 history-based, 2 event-based, 3 warp pools")
+    ap.add_argument("--ctas-per-sm", type=int, default=0,
+                    help="CTAs per SM with --kernel (4 x 256 threads selects the 64-register build)")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batched-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -118,7 +118,7 @@ struct tp_scene {
   bool stage_pending = false;
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
-  int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1};
+  int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
   // CUDA graph of the last graph run and the launch it was captured for
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -598,6 +598,8 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
 struct LaunchCfg {
   int kernel, block, ctas;
   int stage;   // copy the scene tables into shared memory
+  int hi;      // the 64-register build (plain FP32 runs only)
+  int variant() const { return kernel | (hi ? kVariantHighOcc : 0); }
 };
 
 size_t smem_variant(const tp_scene* s, int variant, bool grad, int block, int stage) {
@@ -610,16 +612,27 @@ constexpr uint32_t kStageChoiceBytes = 16 * 1024;
 
 // Completes a launch configuration (CTAs per SM from the occupancy).
 // stage: -1 = stage the tables when they fit (<= kMaxStagedBlob).
-tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c, int stage = -1) {
+// hi: -1 = the 80-register build unless req_ctas asks for more CTAs per SM
+// than it allows and the 64-register build allows more; 0 / 1 = that build.
+tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c, int stage = -1,
+                  int hi = -1) {
   if (stage < 0) stage = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
   if (stage && s->blob_bytes > kMaxStagedBlob) return fail(TP_ERR_INVALID_ARG, "tables too large to stage");
   const int b = req_block > 0 ? req_block : 256;
   if (b % 32 != 0 || b < 32 || b > 256)
     return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
-  int occ = 0;
-  TP_CUDA(occupancy_transport(kernel, s->precision, grad, s->grid_cells > 0, b, smem_variant(s, kernel, grad, b, stage), &occ));
+  const bool can_hi = !grad && s->precision == TP_FP32;
+  if (hi > 0 && !can_hi) return fail(TP_ERR_INVALID_ARG, "the 64-register build serves plain FP32 runs only");
+  int h = hi > 0 ? 1 : 0, occ = 0;
+  const size_t sm = smem_variant(s, kernel, grad, b, stage);
+  TP_CUDA(occupancy_transport(kernel | (h ? kVariantHighOcc : 0), s->precision, grad, s->grid_cells > 0, b, sm, &occ));
+  if (hi < 0 && can_hi && req_ctas > occ) {
+    int occ_hi = 0;
+    TP_CUDA(occupancy_transport(kernel | kVariantHighOcc, s->precision, grad, s->grid_cells > 0, b, sm, &occ_hi));
+    if (occ_hi > occ) { h = 1; occ = occ_hi; }
+  }
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
-  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage};
+  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage, h};
   return TP_OK;
 }
 
@@ -646,8 +659,8 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   cudaError_t e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   const size_t sm = smem_variant(s, c.kernel, grad, c.block, c.stage);
-  if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, c.kernel, grad, grid, c.block, sm, st);
-  else return launch_transport_f32(k, c.kernel, grad, grid, c.block, sm, st);
+  if constexpr (std::is_same<R, double>::value) return launch_transport_f64(k, c.variant(), grad, grid, c.block, sm, st);
+  else return launch_transport_f32(k, c.variant(), grad, grid, c.block, sm, st);
 }
 
 cudaError_t launch_cfg(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
@@ -658,8 +671,10 @@ cudaError_t launch_cfg(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
 
 // Times every candidate (kernel, block size) on up to 2^22 of this run's
 // histories, scoring into scratch tallies, and keeps the fastest.
+// Times every launch candidate on scratch tallies in two rounds: all of them
+// on up to 2^22 histories, then the four fastest on up to 2^25 (short trials
+// of fast scenes are dominated by the launch and the tail of the last wave).
 tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long total, cudaStream_t st) {
-  const unsigned long long trial = std::min(total, 1ull << 22);
   const size_t nb = (size_t)s->n_inst * std::max(1, s->total_bins);
   const size_t per = grad ? 2 + 2 * (size_t)s->n_par : 2;
   double* scratch = nullptr;
@@ -671,39 +686,59 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
             grad ? scratch + (2 + s->n_par) * nb : nullptr, cnt};
   const int cand[][2] = {{TP_KERNEL_EVENT, 256}, {TP_KERNEL_EVENT, 128}, {TP_KERNEL_HISTORY, 128},
                          {TP_KERNEL_HISTORY, 256}, {TP_KERNEL_WARPQ, 256}, {TP_KERNEL_WARPQ, 128}};
+  const int nhi = !grad && s->precision == TP_FP32 ? 2 : 1;   // both register builds
+  const int nstage = s->blob_bytes > kStageChoiceBytes && s->blob_bytes <= kMaxStagedBlob ? 2 : 1;
+  std::vector<LaunchCfg> cfgs;
+  for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]) * nstage * nhi; ++ci) {
+    const int* c = cand[ci / (nstage * nhi)];
+    const int stage = nstage == 2 ? ((ci / nhi) % 2 == 0 ? 1 : 0) : -1;
+    LaunchCfg cfg;
+    if (resolve(s, grad, c[0], c[1], 0, &cfg, stage, ci % nhi) == TP_OK) cfgs.push_back(cfg);   // else: does not fit
+  }
+  if (cfgs.empty()) {
+    cudaFree(scratch);
+    cudaFree(cnt);
+    return fail(TP_ERR_INVALID_ARG, "no launch configuration fits");
+  }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  float best = 1e30f;
-  LaunchCfg pick{0, 0, 0};
   tp_status result = TP_OK;
-  const int nstage = s->blob_bytes > kStageChoiceBytes && s->blob_bytes <= kMaxStagedBlob ? 2 : 1;
-  for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]) * nstage; ++ci) {
-    const int* c = cand[ci / nstage];
-    const int stage = nstage == 2 ? (ci % 2 == 0 ? 1 : 0) : -1;
-    LaunchCfg cfg;
-    if (resolve(s, grad, c[0], c[1], 0, &cfg, stage) != TP_OK) continue;   // does not fit: skip
-    for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
-      cudaEventRecord(a, st);
-      ce = launch_cfg(s, cfg, grad, seed, trial, nullptr, 0, o, st);
-      cudaEventRecord(b, st);
-      if (ce == cudaSuccess) ce = cudaEventSynchronize(b);
-      if (ce != cudaSuccess) break;
+  std::vector<float> ms(cfgs.size(), 1e30f);
+  auto time_all = [&](const std::vector<int>& which, unsigned long long trial) {
+    for (int i : which) {
+      for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
+        cudaEventRecord(a, st);
+        ce = launch_cfg(s, cfgs[i], grad, seed, trial, nullptr, 0, o, st);
+        cudaEventRecord(b, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(b);
+        if (ce != cudaSuccess) return false;
+      }
+      cudaEventElapsedTime(&ms[i], a, b);
     }
-    if (ce != cudaSuccess) { result = fail(TP_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce)); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best) { best = ms; pick = cfg; }
+    return true;
+  };
+  std::vector<int> order(cfgs.size());
+  std::iota(order.begin(), order.end(), 0);
+  const unsigned long long trial1 = std::min(total, 1ull << 22), trial2 = std::min(total, 1ull << 25);
+  bool ok = time_all(order, trial1);
+  if (ok && trial2 > trial1 && order.size() > 1) {
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return ms[x] < ms[y]; });
+    order.resize(std::min<size_t>(4, order.size()));
+    ok = time_all(order, trial2);
   }
+  if (!ok) result = fail(TP_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce));
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(scratch);
   cudaFree(cnt);
   if (result != TP_OK) return result;
-  if (pick.kernel == 0) return fail(TP_ERR_INVALID_ARG, "no launch configuration fits");
+  const int best = *std::min_element(order.begin(), order.end(), [&](int x, int y) { return ms[x] < ms[y]; });
+  const LaunchCfg& pick = cfgs[best];
   s->tuned_kernel[grad] = pick.kernel;
   s->tuned_block[grad] = pick.block;
   s->tuned_stage[grad] = pick.stage;
+  s->tuned_hi[grad] = pick.hi;
   return TP_OK;
 }
 
@@ -713,7 +748,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
 // replay time, so counts and first ids may change between replays.
 tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* r, unsigned long long total,
                     const Outputs& o, cudaStream_t st) {
-  const unsigned long long key[8] = {(unsigned long long)cfg.kernel, (unsigned long long)cfg.block,
+  const unsigned long long key[8] = {(unsigned long long)cfg.variant(), (unsigned long long)cfg.block,
                                      (unsigned long long)(cfg.ctas * 2 + cfg.stage), (unsigned long long)grad, r->seed, total,
                                      (unsigned long long)(uintptr_t)r->records, r->records ? r->n_records : 0};
   if (!s->graph || std::memcmp(key, s->graph_key, sizeof key) != 0) {
@@ -1037,7 +1072,8 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   }
   LaunchCfg cfg;
   tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg,
-                        r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : -1);
+                        r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : -1,
+                        r->kernel == TP_KERNEL_AUTO && r->ctas_per_sm == 0 ? s->tuned_hi[grad] : -1);
   if (e != TP_OK) return e;
   Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
   if (r->use_graph) {

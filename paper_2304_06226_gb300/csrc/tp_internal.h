@@ -124,7 +124,10 @@ struct KParams {
   int* status;
 };
 
-// Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ.
+// Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ,
+// optionally with kVariantHighOcc: the 64-register build of a plain FP32
+// kernel (4 blocks of 256 threads per SM instead of 3).
+constexpr int kVariantHighOcc = 16;
 cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
 cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block,

@@ -1125,8 +1125,8 @@ __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& 
   }
 }
 
-template <typename R, bool GRAD, bool GRID>
-__global__ void __launch_bounds__(256, 3) k_transport(const __grid_constant__ KParams<R> kp) {
+template <typename R, bool GRAD, bool GRID, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
   const uint8_t* base = kp.blob;
@@ -1257,8 +1257,8 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
 }
 
 
-template <typename R, bool GRAD, bool GRID>
-__global__ void __launch_bounds__(256, 3) k_transport_ev(const __grid_constant__ KParams<R> kp) {
+template <typename R, bool GRAD, bool GRID, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
   __shared__ int qcount[kNumQ];
@@ -1452,8 +1452,8 @@ constexpr int kPool = TP_POOL;            // neutrons per warp (a multiple of 32
 static_assert(kPool % 32 == 0, "pool size");
 constexpr int kPoolGroups = kPool / 32;   // pool slots per lane
 
-template <typename R, bool GRAD, bool GRID>
-__global__ void __launch_bounds__(256, 3) k_transport_wq(const __grid_constant__ KParams<R> kp) {
+template <typename R, bool GRAD, bool GRID, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
   const uint8_t* base = kp.blob;
@@ -1682,40 +1682,70 @@ __global__ void k_backward(const double* __restrict__ J, const double* __restric
   }
 }
 
+// Each kernel exists in two register budgets: 80 registers (3 blocks of 256
+// threads per SM) and, for plain FP32 runs, 64 registers (4 blocks; more warps
+// to hide latency, a few more spills).  The flag kVariantHighOcc on the variant
+// selects the second; gradient and FP64 runs always take the first.
+#define TP_KERNEL_TABLE(NAME)                                                                   \
+  template <typename R, bool GRAD, bool GRID, int MINB>                                        \
+  struct NAME##_t {                                                                            \
+    static const void* fn() { return (const void*)NAME<R, GRAD, GRID, MINB>; }                 \
+    static void launch(const KParams<R>& p, int grid, int block, size_t smem, cudaStream_t st) { \
+      NAME<R, GRAD, GRID, MINB><<<grid, block, smem, st>>>(p);                                 \
+    }                                                                                          \
+  };
+TP_KERNEL_TABLE(k_transport)
+TP_KERNEL_TABLE(k_transport_ev)
+TP_KERNEL_TABLE(k_transport_wq)
+#undef TP_KERNEL_TABLE
+template <typename R> struct HistTag { template <bool G, bool D, int M> using k = k_transport_t<R, G, D, M>; };
+template <typename R> struct EvTag { template <bool G, bool D, int M> using k = k_transport_ev_t<R, G, D, M>; };
+template <typename R> struct WqTag { template <bool G, bool D, int M> using k = k_transport_wq_t<R, G, D, M>; };
+
+// Calls F::template run<K>() with K the kernel of (variant, gradients, grid, budget).
+template <typename R, typename F>
+auto with_kernel(int variant, bool grad, bool grid, F&& f) {
+  const bool hi = (variant & kVariantHighOcc) && !grad && sizeof(R) == 4;
+  const int v = variant & ~kVariantHighOcc;
+  auto pick = [&](auto tag) {
+    using T = decltype(tag);
+    if (grad) return grid ? f(typename T::template k<true, true, 3>()) : f(typename T::template k<true, false, 3>());
+    if constexpr (sizeof(R) == 4) {
+      if (hi) return grid ? f(typename T::template k<false, true, 4>()) : f(typename T::template k<false, false, 4>());
+    }
+    return grid ? f(typename T::template k<false, true, 3>()) : f(typename T::template k<false, false, 3>());
+  };
+  if (v == TP_KERNEL_WARPQ) return pick(WqTag<R>{});
+  if (v == TP_KERNEL_EVENT) return pick(EvTag<R>{});
+  return pick(HistTag<R>{});
+}
+
 // kernel pointer for (precision, variant, gradients, grid)
 template <typename R>
 const void* transport_fn(int variant, bool grad, bool grid) {
-  if (variant == TP_KERNEL_WARPQ) {
-    if (grad) return grid ? (const void*)k_transport_wq<R, true, true> : (const void*)k_transport_wq<R, true, false>;
-    return grid ? (const void*)k_transport_wq<R, false, true> : (const void*)k_transport_wq<R, false, false>;
-  }
-  if (variant == TP_KERNEL_EVENT) {
-    if (grad) return grid ? (const void*)k_transport_ev<R, true, true> : (const void*)k_transport_ev<R, true, false>;
-    return grid ? (const void*)k_transport_ev<R, false, true> : (const void*)k_transport_ev<R, false, false>;
-  }
-  if (grad) return grid ? (const void*)k_transport<R, true, true> : (const void*)k_transport<R, true, false>;
-  return grid ? (const void*)k_transport<R, false, true> : (const void*)k_transport<R, false, false>;
+  return with_kernel<R>(variant, grad, grid, [](auto k) { return decltype(k)::fn(); });
 }
 
 template <typename R>
 cudaError_t launch_any(const KParams<R>& p, int variant, bool grad, int grid, int block, size_t smem, cudaStream_t st) {
-  const bool g = p.use_grid != 0;
-  if (variant == TP_KERNEL_WARPQ) {
-    if (grad) { if (g) k_transport_wq<R, true, true><<<grid, block, smem, st>>>(p); else k_transport_wq<R, true, false><<<grid, block, smem, st>>>(p); }
-    else { if (g) k_transport_wq<R, false, true><<<grid, block, smem, st>>>(p); else k_transport_wq<R, false, false><<<grid, block, smem, st>>>(p); }
-  } else if (variant == TP_KERNEL_EVENT) {
-    if (grad) { if (g) k_transport_ev<R, true, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, true, false><<<grid, block, smem, st>>>(p); }
-    else { if (g) k_transport_ev<R, false, true><<<grid, block, smem, st>>>(p); else k_transport_ev<R, false, false><<<grid, block, smem, st>>>(p); }
-  } else {
-    if (grad) { if (g) k_transport<R, true, true><<<grid, block, smem, st>>>(p); else k_transport<R, true, false><<<grid, block, smem, st>>>(p); }
-    else { if (g) k_transport<R, false, true><<<grid, block, smem, st>>>(p); else k_transport<R, false, false><<<grid, block, smem, st>>>(p); }
-  }
+  with_kernel<R>(variant, grad, p.use_grid != 0, [&](auto k) {
+    decltype(k)::launch(p, grid, block, smem, st);
+    return 0;
+  });
   return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit of a kernel only grows, so that every
+// configuration resolved earlier (the autotuner resolves all candidates before
+// timing them) can still be launched.
 cudaError_t occupancy_of(const void* fn, int block, size_t smem, int* ctas) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncAttributes attr;
+  cudaError_t e = cudaFuncGetAttributes(&attr, fn);
   if (e != cudaSuccess) return e;
+  if ((size_t)attr.maxDynamicSharedSizeBytes < smem) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
 }
 
@@ -1734,6 +1764,7 @@ cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size
 }
 
 size_t bank_bytes(int variant, int precision, bool grad, int block) {
+  variant &= ~kVariantHighOcc;
   const size_t ps = precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
   if (variant == TP_KERNEL_EVENT)
     return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;

@@ -126,6 +126,29 @@ def test_launch_shape_does_not_change_results(eng, kernel, block, ctas):
     assert np.allclose(got["sum"], ref["sum"], rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_64_register_build_matches_the_80_register_build(eng, orc, kernel):
+    """Asking for 4 blocks of 256 per SM selects the 64-register build of a
+    plain FP32 kernel; it runs the same source, history for history."""
+    n, nrec = 2_000_000, 20_000
+    desc = W.powder(n_histories=n)
+    ref = gpu_run(eng, desc, n, records=nrec, block_size=256, ctas_per_sm=3, kernel=kernel)
+    hi = gpu_run(eng, desc, n, records=nrec, block_size=256, ctas_per_sm=4, kernel=kernel)
+    assert ref["scene"].launch() == (kernel, 256, 3)
+    assert hi["scene"].launch() == (kernel, 256, 4)
+    a, b = ref["records"], hi["records"]
+    same = (a["end"] == b["end"]) & (a["nscat"] == b["nscat"])
+    assert same.mean() >= 0.999
+    assert np.allclose(a["final_pos"][same], b["final_pos"][same], rtol=1e-4, atol=1e-3)
+    m1, e1 = stats(ref["raw"]["sum"], ref["raw"]["sumsq"], n)
+    m2, e2 = stats(hi["raw"]["sum"], hi["raw"]["sumsq"], n)
+    assert abs(m1.sum() - m2.sum()) <= 1e-4 * m1.sum()
+    o = orc.OracleScene(desc).run(n)
+    m3, e3 = stats(o["sum"], o["sumsq"], n)
+    ok, info = compare_tallies(m2, e2, m3, e3)
+    assert ok, info
+
+
 @pytest.mark.parametrize("n", [0, 1, 31, 33])
 def test_tiny_and_empty_runs(eng, orc, n):
     desc = W.slab(g=1.0, n_histories=max(n, 1), precision="f64")
