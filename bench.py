@@ -35,11 +35,11 @@ POWDER_N = 100_000_000
 # ncu smsp__thread_inst_executed.sum / histories on a small case of each
 # workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
 # the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4126, "guide": 2162, "imaging": 3621, "slab": 5638, "batched": 13454,
-                    "chopper": 1880}
+INST_PER_HISTORY = {"powder": 4243, "guide": 2213, "imaging": 3679, "slab": 5818, "batched": 13316,
+                    "chopper": 1879, "total_scattering": 3478}
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
-TRAFFIC_PER_LAUNCH = {("powder", 3): 827648 + 247808, ("batched", 2): 59525888 + 31343104}
+TRAFFIC_PER_LAUNCH = {("powder", 3): 164352 + 24178176, ("batched", 2): 59709440 + 28421376}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
