@@ -1229,10 +1229,11 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
 // per thread, regrouped every event by what each neutron needs next.  Every
 // iteration builds, with warp ballots, one queue per event type -- new history,
 // advance inside a primitive, advance in the world region, collision -- and
-// runs the queues one after the other with consecutive threads taking
-// consecutive entries, so that the warps of a phase all run the same code.  An
-// advance that reaches a boundary crosses it in the same pass (inside a
-// primitive every crossing is an exit, in the world region an entry).
+// hands queue entries to consecutive threads, so that a warp runs one kind of
+// event.  Gradient runs take the queues one after the other; plain runs take
+// all of them in one phase (see the kernel).  An advance that reaches a
+// boundary crosses it in the same pass (inside a primitive every crossing is
+// an exit, in the world region an entry).
 // ---------------------------------------------------------------------------
 enum { EV_EMPTY = 0, EV_ADV = 1, EV_COLL = 2 };
 enum { Q_EMPTY = 0, Q_ADVP, Q_ADVW, Q_COLL, kNumQ };
@@ -1256,14 +1257,106 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
   *dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
 }
 
+// The per-slot steps of the regrouping kernels.  A bank (event kernel) or pool
+// (warp-pool kernel) holds one neutron per slot with its next event in pend[];
+// in gradient runs a primary that made a radius-derivative secondary waits in
+// park[] while the secondary runs in its slot.
+
+// A new history with global index g into `slot`.  Returns -1 if it ended at
+// the source, else 1 if it starts inside a primitive, 0 in the world region.
+template <typename R>
+__device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V, Particle<R>* bank, int* pend,
+                                          int slot, unsigned long long g, unsigned long long* cnt) {
+  Particle<R> P;
+  int lo = 0, hi = kp.n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  P.inst = (uint32_t)lo;
+  P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
+  R ip[kMaxPar], dR;
+  load_params(kp, P.inst, ip, &dR);
+  cnt[C_HIST]++;
+  int end = -1;
+  if (!source(kp, V, P, dR, &end)) {
+    if (end == END_LOST) cnt[C_LOST]++;
+    finish(kp, P, end);
+    return -1;
+  }
+  bank[slot] = P;
+  pend[slot] = EV_ADV;
+  return P.vol >= 0 ? 1 : 0;
+}
+
+// Advance the neutron of `slot` and, if it reaches a boundary, cross it (inside
+// a primitive every crossing is an exit, in the world region an entry; the
+// caller knows which: in_prim).  Returns true if it now waits for a collision.
+template <typename R, bool GRAD, bool GRID>
+__device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
+                                             Particle<R>* park, int* pend, int* parked, int slot, bool in_prim,
+                                             unsigned long long* cnt) {
+  Particle<R> P = bank[slot];
+  R ip[kMaxPar], dR;
+  load_params(kp, P.inst, ip, &dR);
+  Adv<R> a;
+  bool spawn = false, coll = false;
+  Particle<R> S;
+  int end;
+  if (in_prim) {
+    end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
+    if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+  } else {
+    end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
+    if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+  }
+  if (end == kOutColl) {
+    pend[slot] = EV_COLL;
+    coll = true;
+  } else {
+    if (end >= 0) finish(kp, P, end);
+    if (GRAD && spawn) {
+      if (end < 0) { park[slot] = P; parked[slot] = 1; }
+      P = S;
+      pend[slot] = EV_ADV;
+    } else if (end >= 0) {
+      if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+      else pend[slot] = EV_EMPTY;
+    } else {
+      pend[slot] = EV_ADV;
+    }
+  }
+  bank[slot] = P;
+  return coll;
+}
+
+// The collision the neutron of `slot` waits for.
+template <typename R, bool GRAD>
+__device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
+                                             Particle<R>* park, int* pend, int* parked, int slot,
+                                             unsigned long long* cnt) {
+  Particle<R> P = bank[slot];
+  R ip[kMaxPar], dR;
+  load_params(kp, P.inst, ip, &dR);
+  const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
+  if (end >= 0) {
+    finish(kp, P, end);
+    if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+    else pend[slot] = EV_EMPTY;
+  } else {
+    pend[slot] = EV_ADV;
+  }
+  bank[slot] = P;
+}
+
 
 template <typename R, bool GRAD, bool GRID, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
-  __shared__ int qcount[kNumQ];
+  __shared__ int qcount[2][kNumQ];   // per iteration parity (plain runs)
   __shared__ unsigned long long claim_base;
-  __shared__ int claim_state;  // 0 work left, 1 exhausted
+  __shared__ int claim_state;        // 0 work left, 1 exhausted
   const int NB = blockDim.x;
   const int tid = threadIdx.x;
   const uint8_t* base = kp.blob;
@@ -1295,139 +1388,119 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
   unsigned long long cnt[kNumCounters];
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+  const int lane = tid & 31;
   pend[tid] = EV_EMPTY;
   parked[tid] = 0;
+  if (tid < 2 * kNumQ) qcount[tid / kNumQ][tid % kNumQ] = 0;
   if (tid == 0) claim_state = 0;
   __syncthreads();
 
-  for (int iter = 0;; ++iter) {
-    // ---- classify ----
-    if (tid < kNumQ) qcount[tid] = 0;
-    __syncthreads();
-    {
-      const int ty = pend[tid];
-      q_push(qlist + Q_EMPTY * NB, &qcount[Q_EMPTY], ty == EV_EMPTY, tid);
-      bool inprim = false;
-      if (ty == EV_ADV) inprim = bank[tid].vol >= 0;
-      q_push(qlist + Q_ADVP * NB, &qcount[Q_ADVP], ty == EV_ADV && inprim, tid);
-      q_push(qlist + Q_ADVW * NB, &qcount[Q_ADVW], ty == EV_ADV && !inprim, tid);
-    }
-    __syncthreads();
-    // ---- refill empty slots with new histories ----
-    const int n_empty = qcount[Q_EMPTY];
-    if (tid == 0) {
-      claim_base = kp.total;
-      if (n_empty > 0 && claim_state == 0) {
-        const unsigned long long b = atomicAdd(kp.work_counter, (unsigned long long)n_empty);
-        claim_base = b;
-        if (b + n_empty >= kp.total) claim_state = 1;
+  if constexpr (GRAD) {
+    // Gradient runs: the queues one after the other (refill, advance in a
+    // primitive, advance in the world region, collision), consecutive threads
+    // on consecutive entries, so that all warps of a phase run the same code:
+    // the interface terms and secondaries make the advance large, and a phase
+    // keeps the instructions the SM runs at once few.
+    int* qc = qcount[0];
+    for (;;) {
+      if (tid < kNumQ) qc[tid] = 0;
+      __syncthreads();
+      {
+        const int ty = pend[tid];
+        const bool inprim = ty == EV_ADV && bank[tid].vol >= 0;
+        q_push(qlist + Q_EMPTY * NB, &qc[Q_EMPTY], ty == EV_EMPTY, tid);
+        q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], ty == EV_ADV && inprim, tid);
+        q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], ty == EV_ADV && !inprim, tid);
       }
-    }
-    __syncthreads();
-    {
-      bool born = false, inprim = false;
-      int slot = 0;
-      if (tid < n_empty) {
-        slot = qlist[Q_EMPTY * NB + tid];
-        const unsigned long long g = claim_base + tid;
-        if (g < kp.total) {
-          Particle<R> P;
-          int lo = 0, hi = kp.n_inst - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
-          }
-          P.inst = (uint32_t)lo;
-          P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
-          R ip[kMaxPar], dR;
-          load_params(kp, P.inst, ip, &dR);
-          cnt[C_HIST]++;
-          int end = -1;
-          born = source(kp, V, P, dR, &end);
-          if (!born) {
-            if (end == END_LOST) cnt[C_LOST]++;
-            finish(kp, P, end);
-          } else {
-            inprim = P.vol >= 0;
-            bank[slot] = P;
-            pend[slot] = EV_ADV;
-          }
+      __syncthreads();
+      const int n_empty = qc[Q_EMPTY];
+      if (tid == 0) {
+        claim_base = kp.total;
+        if (n_empty > 0 && claim_state == 0) {
+          const unsigned long long b = atomicAdd(kp.work_counter, (unsigned long long)n_empty);
+          claim_base = b;
+          if (b + n_empty >= kp.total) claim_state = 1;
         }
       }
-      q_push(qlist + Q_ADVP * NB, &qcount[Q_ADVP], born && inprim, slot);
-      q_push(qlist + Q_ADVW * NB, &qcount[Q_ADVW], born && !inprim, slot);
-    }
-    __syncthreads();
-    const int n_advp = qcount[Q_ADVP], n_advw = qcount[Q_ADVW];
-    if (n_advp + n_advw == 0 && claim_state == 1) break;   // uniform: shared values
-    // ---- advance, then cross at once (inside primitives every crossing is an
-    //      exit, in the world region an entry); collisions are queued ----
+      __syncthreads();
+      {
+        int born = -1, slot = 0;
+        if (tid < n_empty) {
+          slot = qlist[Q_EMPTY * NB + tid];
+          const unsigned long long g = claim_base + tid;
+          if (g < kp.total) born = slot_start(kp, V, bank, pend, slot, g, cnt);
+        }
+        q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], born == 1, slot);
+        q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], born == 0, slot);
+      }
+      __syncthreads();
+      const int n_advp = qc[Q_ADVP], n_advw = qc[Q_ADVW];
+      if (n_advp + n_advw == 0 && claim_state == 1) break;   // uniform: shared values
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      const int n = pass == 0 ? n_advp : n_advw;
-      const unsigned short* L = qlist + (pass == 0 ? Q_ADVP : Q_ADVW) * NB;
-      int slot = 0;
-      bool coll = false;
-      if (tid < n) {
-        slot = L[tid];
-        Particle<R> P = bank[slot];
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        Adv<R> a;
-        bool spawn = false;
-        Particle<R> S;
-        int end;
-        if (pass == 0) {
-          end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
-          if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
-        } else {
-          end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
-          if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+      for (int pass = 0; pass < 2; ++pass) {
+        const int n = pass == 0 ? n_advp : n_advw;
+        int slot = 0;
+        bool coll = false;
+        if (tid < n) {
+          slot = qlist[(pass == 0 ? Q_ADVP : Q_ADVW) * NB + tid];
+          coll = slot_advance<R, GRAD, GRID>(kp, V, bank, park, pend, parked, slot, pass == 0, cnt);
         }
-        if (end == kOutColl) {
-          pend[slot] = EV_COLL;
-          coll = true;
-        } else {
-          if (end >= 0) finish(kp, P, end);
-          if (GRAD && spawn) {
-            if (end < 0) { park[slot] = P; parked[slot] = 1; }
-            P = S;
-            pend[slot] = EV_ADV;
-          } else if (end >= 0) {
-            if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-            else pend[slot] = EV_EMPTY;
-          } else {
-            pend[slot] = EV_ADV;
-          }
-        }
-        bank[slot] = P;
+        q_push(qlist + Q_COLL * NB, &qc[Q_COLL], coll, slot);
       }
-      q_push(qlist + Q_COLL * NB, &qcount[Q_COLL], tid < n && coll, slot);
+      __syncthreads();
+      if (tid < qc[Q_COLL]) slot_collide<R, GRAD>(kp, V, bank, park, pend, parked, qlist[Q_COLL * NB + tid], cnt);
+      __syncthreads();
     }
-    __syncthreads();
-    // ---- collisions ----
-    {
-      const int n = qcount[Q_COLL];
-      if (tid < n) {
-        const int slot = qlist[Q_COLL * NB + tid];
-        Particle<R> P = bank[slot];
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
-        if (end >= 0) {
-          finish(kp, P, end);
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
-        } else {
-          pend[slot] = EV_ADV;
-        }
-        bank[slot] = P;
+  } else {
+    // Plain runs: one work phase per iteration in which thread t takes the
+    // t-th entry of the concatenated queues [advance in a primitive | advance
+    // in the world region | collision | refill], so that every thread of the
+    // block has a slot and each warp runs one kind of event (but those at the
+    // joins).  Two barriers per iteration; the counts alternate between two
+    // buffers so that a reset never meets a reader.
+    for (int iter = 0;; ++iter) {
+      int* qc = qcount[iter & 1];
+      bool exhausted;
+      {
+        const int ty = pend[tid];
+        const bool inprim = ty == EV_ADV && bank[tid].vol >= 0;
+        q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], ty == EV_ADV && inprim, tid);
+        q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], ty == EV_ADV && !inprim, tid);
+        q_push(qlist + Q_COLL * NB, &qc[Q_COLL], ty == EV_COLL, tid);
+        q_push(qlist + Q_EMPTY * NB, &qc[Q_EMPTY], ty == EV_EMPTY, tid);
+        if (tid < kNumQ) qcount[(iter + 1) & 1][tid] = 0;   // last read in the previous work phase
+        exhausted = claim_state != 0;                       // last written in the previous work phase
       }
+      __syncthreads();
+      const int nA = qc[Q_ADVP], nW = qc[Q_ADVW], nC = qc[Q_COLL], nE = qc[Q_EMPTY];
+      if (nA + nW + nC == 0 && exhausted) break;   // uniform: shared values read before any write
+      int t = tid;
+      if (t < nA + nW) {
+        const bool in_prim = t < nA;
+        slot_advance<R, GRAD, GRID>(kp, V, bank, park, pend, parked,
+                                    in_prim ? qlist[Q_ADVP * NB + t] : qlist[Q_ADVW * NB + t - nA], in_prim, cnt);
+      } else if ((t -= nA + nW) < nC) {
+        slot_collide<R, GRAD>(kp, V, bank, park, pend, parked, qlist[Q_COLL * NB + t], cnt);
+      } else {
+        t -= nC;
+      }
+      // refill: the threads past the live queues take new histories, one claim per warp
+      const bool want = tid >= nA + nW + nC && t < nE && !exhausted;
+      const unsigned m = __ballot_sync(kFull, want);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long g = 0;
+        if (lane == leader) g = atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
+        g = __shfl_sync(kFull, g, leader) + __popc(m & ((1u << lane) - 1u));
+        if (want) {
+          if (g < kp.total) slot_start(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
+          else claim_state = 1;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   // ---- counters ----
-  const int lane = tid & 31;
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) {
     unsigned long long v = cnt[i];
@@ -1556,82 +1629,15 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
           chunk_end = min(b + (unsigned long long)kp.chunk, kp.total);
         }
         const int avail = (int)min((unsigned long long)(n - taken), chunk_end - chunk_next);
-        if (lane >= taken && lane < taken + avail) {
-          const unsigned long long g = chunk_next + (lane - taken);
-          Particle<R> P;
-          int lo = 0, hi = kp.n_inst - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (kp.inst_prefix[mid] <= g) lo = mid; else hi = mid - 1;
-          }
-          P.inst = (uint32_t)lo;
-          P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
-          R ip[kMaxPar], dR;
-          load_params(kp, P.inst, ip, &dR);
-          cnt[C_HIST]++;
-          int end = -1;
-          if (source(kp, V, P, dR, &end)) {
-            pool[slot] = P;
-            pend[slot] = EV_ADV;
-          } else {
-            if (end == END_LOST) cnt[C_LOST]++;
-            finish(kp, P, end);
-          }
-        }
+        if (lane >= taken && lane < taken + avail)
+          slot_start(kp, V, pool, pend, slot, chunk_next + (lane - taken), cnt);
         chunk_next += avail;
         taken += avail;
       }
     } else if (q == Q_ADVP || q == Q_ADVW) {
-      // advance, and cross at once: inside a primitive every crossing is an
-      // exit, in the world region an entry, so the lanes stay on one path;
-      // collisions wait in their own queue
-      if (slot >= 0) {
-        Particle<R> P = pool[slot];
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        Adv<R> a;
-        bool spawn = false;
-        Particle<R> S;
-        int end;
-        if (q == Q_ADVP) {
-          end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
-          if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
-        } else {
-          end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
-          if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
-        }
-        if (end == kOutColl) {
-          pend[slot] = EV_COLL;
-        } else {
-          if (end >= 0) finish(kp, P, end);
-          if (GRAD && spawn) {
-            if (end < 0) { park[slot] = P; parked[slot] = 1; }
-            P = S;
-            pend[slot] = EV_ADV;
-          } else if (end >= 0) {
-            if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-            else pend[slot] = EV_EMPTY;
-          } else {
-            pend[slot] = EV_ADV;
-          }
-        }
-        pool[slot] = P;
-      }
+      if (slot >= 0) slot_advance<R, GRAD, GRID>(kp, V, pool, park, pend, parked, slot, q == Q_ADVP, cnt);
     } else {
-      if (slot >= 0) {
-        Particle<R> P = pool[slot];
-        R ip[kMaxPar], dR;
-        load_params(kp, P.inst, ip, &dR);
-        const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
-        if (end >= 0) {
-          finish(kp, P, end);
-          if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
-          else pend[slot] = EV_EMPTY;
-        } else {
-          pend[slot] = EV_ADV;
-        }
-        pool[slot] = P;
-      }
+      if (slot >= 0) slot_collide<R, GRAD>(kp, V, pool, park, pend, parked, slot, cnt);
     }
     __syncwarp();
   }
