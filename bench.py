@@ -44,6 +44,9 @@ TRAFFIC_PER_LAUNCH = {("powder", 3): 164352 + 24178176, ("batched", 2): 59709440
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
                 "chopper": 2}
+# Workloads whose configuration asks for the adjoint: their step is a run with
+# the score-function accumulators plus the backward contraction.
+GRAD_WORKLOADS = ("batched", "imaging")
 SM_COUNT = 152
 LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
 SM_MAX_MHZ = 2070.0
@@ -58,7 +61,8 @@ def workload_desc(name: str):
     if name == "slab":
         return W.slab(g=3.0, n_histories=1_000_000), "slab, bias 3, 1e6 histories, FP64 transport"
     if name == "imaging":
-        return W.imaging(n_histories=1_000_000_000), "CSG imaging 1000 primitives, 512^2 PSD, 1e9 histories, FP32 transport"
+        return W.imaging(n_histories=1_000_000_000), ("CSG imaging 1000 primitives, 512^2 PSD, 1e9 histories, FP32 "
+                                                      "transport, adjoint w.r.t. the 3 material densities")
     if name == "total_scattering":
         return W.total_scattering(n_histories=100_000_000), ("total scattering: pencil on a 1.2 cm fcc-powder sphere, 4 pi "
                                                              "detector, Q per scattering order, 1e8 histories, FP32 transport")
@@ -147,7 +151,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     desc, label = workload_desc(args.workload)
-    grad = args.workload == "batched"
+    grad = args.workload in GRAD_WORKLOADS
     if args.histories:
         if grad:   # keep the instance mix, scale the counts to the requested total
             c = desc["instances"]["counts"].astype(np.float64)
@@ -278,7 +282,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             "batched_s_to_eps_per_instance": batched.get("s_to_eps_per_instance"),
         }
     if args.cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, desc, n)
+        line["cpu_baseline"] = cpu_baseline(args, desc, n, grad=grad)
     sc.close()
     return line
 
@@ -329,22 +333,43 @@ def run_batched(args, W, Scene, torch) -> dict:
                          "kernel": "transport forward with score-function accumulators"},
             "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
             "rel_stderr_total_median_instance": rel,
-            "s_to_eps_per_instance": (rel / 1e-3) ** 2 * N / (hist_s / len(counts))}
+            "s_to_eps_per_instance": (rel / 1e-3) ** 2 * N / (hist_s / len(counts)),
+            **({"cpu_baseline": cpu_baseline(args, desc, total, grad=True)} if args.cpu_baseline else {})}
 
 
-def cpu_baseline(args, desc, n_full) -> dict:
-    """The CPU oracle on the host cores, on a bounded sample of the workload."""
+def cpu_baseline(args, desc, n_full, grad: bool = False) -> dict:
+    """The CPU oracle on the host cores, on a bounded sample of the workload:
+    a pilot run sets the sample to about args.cpu_seconds of CPU work.  With
+    grad, every instance runs a share of the sample in proportion to its
+    history count, with the score-function accumulators."""
+    import numpy as np
     from oracle.oracle import OracleScene
     cores = os.cpu_count() or 1
     sc = OracleScene(desc)
-    sample = args.cpu_sample
-    sc.run(min(100_000, sample), threads=cores)       # warm the library
+    counts = np.asarray(desc["instances"]["counts"], dtype=np.float64)
+
+    def run(total):
+        if not grad:
+            sc.run(total, threads=cores)
+            return total
+        share = np.maximum(1, np.rint(total * counts / counts.sum())).astype(np.int64)
+        for q, m in enumerate(share):
+            sc.run(int(m), inst=q, threads=cores, want_grad=True)
+        return int(share.sum())
+
+    pilot = max(10_000, min(args.cpu_sample // 40, 1_000_000))
+    run(min(100_000, pilot))                 # warm the library
     t0 = time.perf_counter()
-    sc.run(sample, threads=cores)
+    done = run(pilot)
+    rate = done / (time.perf_counter() - t0)
+    sample = int(min(max(rate * args.cpu_seconds, pilot), args.cpu_sample, n_full))
+    t0 = time.perf_counter()
+    sample = run(sample)
     dt = time.perf_counter() - t0
+    what = (f"{sample} histories of the {n_full}-history workload, a share of every instance in proportion "
+            f"to its count, with gradients" if grad else f"the first {sample} histories of the {n_full}-history workload")
     return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} histories of the {n_full}-history workload, FP64, {cores} threads",
-            "seconds": dt}
+            "sample": f"{what}; FP64, {cores} threads", "seconds": dt}
 
 
 def run_reference(args, rank: int) -> dict | None:
@@ -403,7 +428,8 @@ def main() -> None:
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batched-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-sample", type=int, default=40_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000_000, help="most histories of the CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU work the baseline sample is sized to")
     ap.add_argument("--ref-sample", type=int, default=10_000_000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
