@@ -803,15 +803,18 @@ static void history(ctx* c, uint64_t hid, or_record* rec) {
   }
   P.w = 1.0;
   P.sub0 = 0u;
+  /* a history can end at its source: the record then holds the birth point */
+  if (rec)
+    for (int i = 0; i < 3; ++i) rec->final_pos[i] = P.r[i];
   if (g->has_aperture &&
       (fabs(P.r[0] - g->c[0]) > g->aperture[0] || fabs(P.r[1] - g->c[1]) > g->aperture[1])) {
     if (rec) { rec->end = OR_END_APERTURE; rec->w_final = 0.0; }
     return;
   }
   P.vol = locate(s, c->ip, P.r);
-  if (P.vol == -2) { if (rec) rec->end = OR_END_LOST; acc->counters[5]++; return; }
+  if (P.vol == -2) { if (rec) { rec->end = OR_END_LOST; rec->w_final = P.w; } acc->counters[5]++; return; }
   if (P.vol >= 0 && s->prims[P.vol].role != OR_ROLE_BULK) {
-    if (rec) rec->end = OR_END_BLACK;
+    if (rec) { rec->end = OR_END_BLACK; rec->w_final = P.w; }
     return;
   }
   uint32_t nsec = 0;
