@@ -248,7 +248,15 @@ typedef struct {
  *   (kernel, block, CTAs, gradients, seed, total histories, records) and
  *   replayed afterwards; history counts and first ids may change between
  *   replays (they are read from the scene's pinned staging buffer).
- * records: device array of n_records tp_record, or NULL. */
+ * records: device array of n_records tp_record, or NULL.
+ * secondaries (gradient runs with a radius parameter): the radius-derivative
+ *   secondaries are transported 1 = where they are made, while their primary
+ *   waits, or 2 = queued in device memory and transported by a second pass of
+ *   the plain kernel, the run going through the histories in chunks whose
+ *   secondaries fit the queue (at most 2^25 records, sized at the first such
+ *   run; a secondary finding the queue full is transported in place); 0 =
+ *   chosen by the autotuner with kernel 0, else 1.  Results do not depend on
+ *   the choice (each secondary has its own random numbers). */
 typedef struct {
   uint64_t seed;
   const uint64_t* n_histories;
@@ -261,6 +269,7 @@ typedef struct {
   uint64_t n_records;
   int kernel;
   int use_graph;
+  int secondaries;
 } tp_run;
 
 enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2, TP_KERNEL_WARPQ = 3 };

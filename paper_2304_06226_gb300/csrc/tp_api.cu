@@ -70,6 +70,15 @@ struct Mat {
 
 }  // namespace
 
+// A launch configuration: kernel variant, block size, CTAs per SM and options.
+struct LaunchCfg {
+  int kernel, block, ctas;
+  int stage;   // copy the scene tables into shared memory
+  int hi;      // the 64-register build (plain FP32 runs only)
+  int defer;   // gradient runs: secondaries queued and transported in a second pass
+  int variant() const { return kernel | (hi ? kVariantHighOcc : 0); }
+};
+
 struct tp_scene {
   int device = 0;
   int sm_count = 0;
@@ -119,6 +128,12 @@ struct tp_scene {
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
+  int tuned_defer = 0;   // gradient runs: secondaries queued for a second pass
+  // queue of radius-derivative secondaries for the second pass (gradient runs)
+  uint8_t* d_sec = nullptr;
+  unsigned long long* d_sec_count = nullptr;
+  unsigned long long sec_cap = 0;
+  LaunchCfg sec_cfg{0, 0, 0, 0, 0, 0};   // the second pass (plain warp-pool kernel)
   // CUDA graph of the last graph run and the launch it was captured for
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -595,13 +610,6 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
   return TP_OK;
 }
 
-struct LaunchCfg {
-  int kernel, block, ctas;
-  int stage;   // copy the scene tables into shared memory
-  int hi;      // the 64-register build (plain FP32 runs only)
-  int variant() const { return kernel | (hi ? kVariantHighOcc : 0); }
-};
-
 size_t smem_variant(const tp_scene* s, int variant, bool grad, int block, int stage) {
   return (stage ? align16(s->blob_bytes) : 0) + align16(bank_bytes(variant, s->precision, grad, block));
 }
@@ -632,7 +640,7 @@ tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_cta
     if (occ_hi > occ) { h = 1; occ = occ_hi; }
   }
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
-  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage, h};
+  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage, h, 0};
   return TP_OK;
 }
 
@@ -641,11 +649,19 @@ struct Outputs {
   unsigned long long* counters;
 };
 
+// One launch.  sec_mode: see KParams; index_base: global index of its first
+// history (a chunk of a longer run).
 template <typename R>
 cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
-                       tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st) {
+                       tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st,
+                       int sec_mode = 0, unsigned long long index_base = 0) {
   KParams<R> k{};
   fill_common(s, k);
+  k.sec_mode = sec_mode;
+  k.sec_buf = s->d_sec;
+  k.sec_count = s->d_sec_count;
+  k.sec_cap = s->sec_cap;
+  k.index_base = index_base;
   k.key0 = (uint32_t)(seed & 0xffffffffu);
   k.key1 = (uint32_t)(seed >> 32);
   k.total = total;
@@ -655,7 +671,7 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   k.stage_blob = c.stage;
   const int grid = s->sm_count * c.ctas;
   const long long warps = (long long)grid * (c.block / 32);
-  k.chunk = (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
+  k.chunk = sec_mode == 2 ? 16 : (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
   cudaError_t e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   const size_t sm = smem_variant(s, c.kernel, grad, c.block, c.stage);
@@ -663,10 +679,58 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   else return launch_transport_f32(k, c.variant(), grad, grid, c.block, sm, st);
 }
 
+// Histories a chunk of a queued-secondaries run may hold: the queue takes
+// kSecPerHistory secondaries per history (about twice what the densest
+// workloads make); a fuller queue transports the rest in place.
+constexpr unsigned long long kSecPerHistory = 8;
+constexpr unsigned long long kSecCapMin = 1ull << 16, kSecCapMax = 1ull << 25;
+
+// The queue of secondaries for runs of up to `total` histories (allocated
+// outside any stream capture; a larger one drops the captured graph).
+tp_status ensure_sec(tp_scene* s, unsigned long long total) {
+  unsigned long long want = kSecCapMin;
+  while (want < kSecCapMax && want < kSecPerHistory * total) want <<= 1;
+  if (s->sec_cfg.kernel == 0) {
+    tp_status st = resolve(s, false, TP_KERNEL_WARPQ, 256, 0, &s->sec_cfg, -1, s->precision == TP_FP32 ? 1 : 0);
+    if (st != TP_OK) return st;
+  }
+  if (s->d_sec && s->sec_cap >= want) return TP_OK;
+  if (s->stage_pending) { TP_CUDA(cudaEventSynchronize(s->stage_done)); s->stage_pending = false; }
+  TP_CUDA(cudaDeviceSynchronize());
+  cudaFree(s->d_sec);
+  s->d_sec = nullptr;
+  s->sec_cap = 0;
+  if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+  TP_CUDA(cudaMalloc(&s->d_sec, want * particle_bytes(s->precision)));
+  if (!s->d_sec_count) TP_CUDA(cudaMalloc(&s->d_sec_count, sizeof(unsigned long long)));
+  s->sec_cap = want;
+  return TP_OK;
+}
+
+// The launch (or, for queued secondaries, the sequence of launches) of a run:
+// chunks of histories whose secondaries fit the queue, each followed by a
+// second pass of the plain warp-pool kernel over the queue.
+template <typename R>
+cudaError_t launch_run(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
+                       tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st) {
+  if (!grad || !c.defer) return launch_one<R>(s, c, grad, seed, total, records, n_records, o, st);
+  if (!s->d_sec || s->sec_cfg.kernel == 0) return cudaErrorInvalidValue;   // ensure_sec comes first
+  const LaunchCfg& sc = s->sec_cfg;
+  const unsigned long long chunk = std::max(1ull, s->sec_cap / kSecPerHistory);
+  for (unsigned long long c0 = 0; c0 < total; c0 += chunk) {
+    const unsigned long long n = std::min(chunk, total - c0);
+    cudaError_t e = cudaMemsetAsync(s->d_sec_count, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_one<R>(s, c, true, seed, n, records, n_records, o, st, 1, c0);
+    if (e == cudaSuccess) e = launch_one<R>(s, sc, false, seed, 0, nullptr, 0, o, st, 2, 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_cfg(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed, unsigned long long total,
                        tp_record* records, unsigned long long n_records, const Outputs& o, cudaStream_t st) {
-  if (s->precision == TP_FP64) return launch_one<double>(s, c, grad, seed, total, records, n_records, o, st);
-  return launch_one<float>(s, c, grad, seed, total, records, n_records, o, st);
+  if (s->precision == TP_FP64) return launch_run<double>(s, c, grad, seed, total, records, n_records, o, st);
+  return launch_run<float>(s, c, grad, seed, total, records, n_records, o, st);
 }
 
 // Times every candidate (kernel, block size) on up to 2^22 of this run's
@@ -693,7 +757,12 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
     const int* c = cand[ci / (nstage * nhi)];
     const int stage = nstage == 2 ? ((ci / nhi) % 2 == 0 ? 1 : 0) : -1;
     LaunchCfg cfg;
-    if (resolve(s, grad, c[0], c[1], 0, &cfg, stage, ci % nhi) == TP_OK) cfgs.push_back(cfg);   // else: does not fit
+    if (resolve(s, grad, c[0], c[1], 0, &cfg, stage, ci % nhi) != TP_OK) continue;   // does not fit
+    cfgs.push_back(cfg);
+    if (grad && s->d_sec) {   // and with the secondaries queued for a second pass
+      cfg.defer = 1;
+      cfgs.push_back(cfg);
+    }
   }
   if (cfgs.empty()) {
     cudaFree(scratch);
@@ -739,6 +808,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   s->tuned_block[grad] = pick.block;
   s->tuned_stage[grad] = pick.stage;
   s->tuned_hi[grad] = pick.hi;
+  if (grad) s->tuned_defer = pick.defer;
   return TP_OK;
 }
 
@@ -749,7 +819,8 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
 tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* r, unsigned long long total,
                     const Outputs& o, cudaStream_t st) {
   const unsigned long long key[8] = {(unsigned long long)cfg.variant(), (unsigned long long)cfg.block,
-                                     (unsigned long long)(cfg.ctas * 2 + cfg.stage), (unsigned long long)grad, r->seed, total,
+                                     (unsigned long long)(cfg.ctas * 4 + cfg.stage * 2 + cfg.defer), (unsigned long long)grad,
+                                     r->seed, total,
                                      (unsigned long long)(uintptr_t)r->records, r->records ? r->n_records : 0};
   if (!s->graph || std::memcmp(key, s->graph_key, sizeof key) != 0) {
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
@@ -1058,6 +1129,12 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   }
   s->h_stage[s->n_inst] = total;
   if (total == 0) return TP_OK;
+  if (r->secondaries < 0 || r->secondaries > 2) return fail(TP_ERR_INVALID_ARG, "secondaries %d", r->secondaries);
+  const bool tune = r->kernel == TP_KERNEL_AUTO && s->tuned_kernel[grad] == 0;
+  if (grad && (r->secondaries == 2 || (r->secondaries == 0 && (tune || (r->kernel == TP_KERNEL_AUTO && s->tuned_defer))))) {
+    tp_status e = ensure_sec(s, total);   // before any capture: it may allocate
+    if (e != TP_OK) return e;
+  }
   int kernel = r->kernel, block = r->block_size;
   if (kernel == TP_KERNEL_AUTO) {
     if (s->tuned_kernel[grad] == 0) {
@@ -1066,6 +1143,12 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
       TP_CUDA(cudaMemcpyAsync(s->d_first, s->h_stage + s->n_inst + 1, s->n_inst * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
       tp_status e = autotune(s, grad, r->seed, total, st);
       if (e != TP_OK) return e;
+      if (grad && !s->tuned_defer && r->secondaries != 2 && s->d_sec) {   // not needed: give it back
+        TP_CUDA(cudaStreamSynchronize(st));
+        cudaFree(s->d_sec);
+        s->d_sec = nullptr;
+        s->sec_cap = 0;
+      }
     }
     kernel = s->tuned_kernel[grad];
     if (block == 0) block = s->tuned_block[grad];
@@ -1075,6 +1158,7 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
                         r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : -1,
                         r->kernel == TP_KERNEL_AUTO && r->ctas_per_sm == 0 ? s->tuned_hi[grad] : -1);
   if (e != TP_OK) return e;
+  if (grad) cfg.defer = r->secondaries == 2 || (r->secondaries == 0 && r->kernel == TP_KERNEL_AUTO && s->tuned_defer);
   Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
   if (r->use_graph) {
     e = run_graph(s, cfg, grad, r, total, o, st);
@@ -1202,6 +1286,7 @@ void tp_destroy_scene(tp_scene* s) {
   cudaFree(s->d_sum); cudaFree(s->d_sumsq); cudaFree(s->d_J); cudaFree(s->d_J2);
   cudaFree(s->d_prefix); cudaFree(s->d_first); cudaFree(s->d_params); cudaFree(s->d_aux);
   cudaFree(s->d_work); cudaFree(s->d_counters); cudaFree(s->d_status);
+  cudaFree(s->d_sec); cudaFree(s->d_sec_count);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->h_aux) cudaFreeHost(s->h_aux);
   if (s->stage_done) cudaEventDestroy(s->stage_done);

@@ -112,6 +112,15 @@ struct KParams {
   unsigned long long total;
   unsigned long long* work_counter;
   int chunk;  // histories a warp claims at once
+  unsigned long long index_base;  // global index of claim 0 (one chunk of a longer run)
+  // Radius-derivative secondaries of gradient runs: 0 = transported where
+  // they are made; 1 = appended to sec_buf (transported in place only when it
+  // is full); 2 = this launch transports the sec_buf records instead of new
+  // histories.
+  int sec_mode;
+  uint8_t* sec_buf;                 // [sec_cap] neutron records
+  unsigned long long* sec_count;    // records appended (may pass sec_cap)
+  unsigned long long sec_cap;
   // outputs
   double* sum;    // [n_inst][total_bins]
   double* sumsq;
@@ -134,6 +143,8 @@ cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool gra
                                  size_t smem, cudaStream_t st);
 // Shared memory of the neutron bank of a variant (added to the staged tables).
 size_t bank_bytes(int variant, int precision, bool grad, int block);
+// Bytes of one queued neutron record (sec_buf).
+size_t particle_bytes(int precision);
 cudaError_t occupancy_transport(int variant, int precision, bool grad, bool use_grid, int block, size_t smem,
                                 int* ctas);
 cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas);

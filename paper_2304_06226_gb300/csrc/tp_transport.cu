@@ -573,7 +573,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
           agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
         }
       }
-    } else if (GRAD && kp.radius_par >= 0) {
+    } else if (kp.radius_par >= 0) {   // a radius-derivative secondary
       agg_add2(kp.J, kp.J2, kp.radius_par * stride + idx, w, w * w);
     }
   }
@@ -1125,6 +1125,25 @@ __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& 
   }
 }
 
+// Histories (or queued secondaries) a launch works through.
+template <typename R>
+__device__ __forceinline__ unsigned long long work_total(const KParams<R>& kp) {
+  if (kp.sec_mode != 2) return kp.total;
+  const unsigned long long n = *kp.sec_count;   // written by the previous launch on the stream
+  return n < kp.sec_cap ? n : kp.sec_cap;
+}
+
+// Appends a radius-derivative secondary to the queue of the second pass;
+// false if the queue is full (the caller then transports it in place).
+template <typename R>
+__device__ __forceinline__ bool sec_push(const KParams<R>& kp, const Particle<R>& S) {
+  if (kp.sec_mode != 1) return false;
+  const unsigned long long i = atomicAdd(kp.sec_count, 1ull);
+  if (i >= kp.sec_cap) return false;
+  reinterpret_cast<Particle<R>*>(kp.sec_buf)[i] = S;
+  return true;
+}
+
 template <typename R, bool GRAD, bool GRID, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -1157,6 +1176,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
   R ip[kMaxPar];
   R dR = R(0);
   bool alive = false, done = false, parked = false;
+  const unsigned long long total = work_total(kp);
   unsigned long long chunk_next = 0, chunk_end = 0;  // warp-uniform
 
   for (;;) {
@@ -1167,17 +1187,23 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
         unsigned long long b = 0;
         if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
         b = __shfl_sync(kFull, b, 0);
-        if (b >= kp.total) {
+        if (b >= total) {
           if (!alive) done = true;
           break;
         }
         chunk_next = b;
-        chunk_end = min(b + (unsigned long long)kp.chunk, kp.total);
+        chunk_end = min(b + (unsigned long long)kp.chunk, total);
       }
       const unsigned avail = (unsigned)min((unsigned long long)__popc(idle), chunk_end - chunk_next);
       const unsigned rank = __popc(idle & lt_mask);
-      if (((idle >> lane) & 1u) && rank < avail) {
-        const unsigned long long g = chunk_next + rank;
+      if (((idle >> lane) & 1u) && rank < avail && kp.sec_mode == 2) {
+        P = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[chunk_next + rank];   // a queued secondary
+#pragma unroll
+        for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)kp.inst_params[(size_t)P.inst * kMaxPar + i];
+        dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
+        alive = true;
+      } else if (((idle >> lane) & 1u) && rank < avail) {
+        const unsigned long long g = chunk_next + rank + kp.index_base;
         // instance of global index g
         int lo = 0, hi = kp.n_inst - 1;
         while (lo < hi) {
@@ -1205,6 +1231,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
       bool spawn = false;
       const int end = step<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, &S, &spawn);
       if (end >= 0) finish(kp, P, end);
+      if (GRAD && spawn && sec_push(kp, S)) spawn = false;
       if (GRAD && spawn) {
         if (end < 0) { park = P; parked = true; }
         P = S;
@@ -1267,6 +1294,13 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
 template <typename R>
 __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V, Particle<R>* bank, int* pend,
                                           int slot, unsigned long long g, unsigned long long* cnt) {
+  if (kp.sec_mode == 2) {   // a queued secondary: it starts where it was made
+    const Particle<R> S = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[g];
+    bank[slot] = S;
+    pend[slot] = EV_ADV;
+    return S.vol >= 0 ? 1 : 0;
+  }
+  g += kp.index_base;
   Particle<R> P;
   int lo = 0, hi = kp.n_inst - 1;
   while (lo < hi) {
@@ -1315,6 +1349,7 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
     coll = true;
   } else {
     if (end >= 0) finish(kp, P, end);
+    if (GRAD && spawn && sec_push(kp, S)) spawn = false;
     if (GRAD && spawn) {
       if (end < 0) { park[slot] = P; parked[slot] = 1; }
       P = S;
@@ -1385,6 +1420,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
   int* parked = pend + NB;
   unsigned short* qlist = reinterpret_cast<unsigned short*>(parked + NB);  // [kNumQ][NB]
 
+  const unsigned long long total = work_total(kp);
   unsigned long long cnt[kNumCounters];
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
@@ -1415,11 +1451,11 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       __syncthreads();
       const int n_empty = qc[Q_EMPTY];
       if (tid == 0) {
-        claim_base = kp.total;
+        claim_base = total;
         if (n_empty > 0 && claim_state == 0) {
           const unsigned long long b = atomicAdd(kp.work_counter, (unsigned long long)n_empty);
           claim_base = b;
-          if (b + n_empty >= kp.total) claim_state = 1;
+          if (b + n_empty >= total) claim_state = 1;
         }
       }
       __syncthreads();
@@ -1428,7 +1464,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         if (tid < n_empty) {
           slot = qlist[Q_EMPTY * NB + tid];
           const unsigned long long g = claim_base + tid;
-          if (g < kp.total) born = slot_start(kp, V, bank, pend, slot, g, cnt);
+          if (g < total) born = slot_start(kp, V, bank, pend, slot, g, cnt);
         }
         q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], born == 1, slot);
         q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], born == 0, slot);
@@ -1493,7 +1529,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         if (lane == leader) g = atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
         g = __shfl_sync(kFull, g, leader) + __popc(m & ((1u << lane) - 1u));
         if (want) {
-          if (g < kp.total) slot_start(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
+          if (g < total) slot_start(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
           else claim_state = 1;
         }
       }
@@ -1558,6 +1594,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
               warp * 2 * kPool;
   int* parked = pend + kPool;
 
+  const unsigned long long total = work_total(kp);
   unsigned long long cnt[kNumCounters];
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
@@ -1624,9 +1661,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
           unsigned long long b = 0;
           if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
           b = __shfl_sync(kFull, b, 0);
-          if (b >= kp.total) { work_left = false; break; }
+          if (b >= total) { work_left = false; break; }
           chunk_next = b;
-          chunk_end = min(b + (unsigned long long)kp.chunk, kp.total);
+          chunk_end = min(b + (unsigned long long)kp.chunk, total);
         }
         const int avail = (int)min((unsigned long long)(n - taken), chunk_end - chunk_next);
         if (lane >= taken && lane < taken + avail)
@@ -1767,6 +1804,10 @@ cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad
 
 cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
   return occupancy_of(transport_fn<float>(variant, grad, use_grid), block, smem, ctas);
+}
+
+size_t particle_bytes(int precision) {
+  return precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
 }
 
 size_t bank_bytes(int variant, int precision, bool grad, int block) {

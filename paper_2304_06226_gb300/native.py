@@ -92,7 +92,7 @@ class tp_run(C.Structure):
                 ("first_history", C.POINTER(C.c_uint64)), ("want_grad", C.c_int),
                 ("stream", C.c_void_p), ("block_size", C.c_int), ("ctas_per_sm", C.c_int),
                 ("records", C.c_void_p), ("n_records", C.c_uint64), ("kernel", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("secondaries", C.c_int)]
 
 
 SCENE_P = C.c_void_p

@@ -278,11 +278,12 @@ def small_batched(n_inst=6, lo=2e4, hi=1e5, precision="f32"):
     return W.batched(n_instances=n_inst, count_lo=lo, count_hi=hi, precision=precision)
 
 
+@pytest.mark.parametrize("secondaries", [1, 2])   # in place, queued for a second pass
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc, kernel):
+def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc, kernel, secondaries):
     desc = small_batched(n_inst=4, lo=3000, hi=8000, precision="f64")
     sc = eng.Scene(desc)
-    sc.run(want_grad=True, kernel=kernel)
+    sc.run(want_grad=True, kernel=kernel, secondaries=secondaries)
     torch.cuda.synchronize()
     osc = orc.OracleScene(desc)
     for q in range(4):
@@ -293,11 +294,12 @@ def test_batched_fp64_histories_and_gradient_accumulators_match(eng, orc, kernel
         assert np.allclose(g["J"], o["J"], rtol=1e-7, atol=1e-8), q
 
 
+@pytest.mark.parametrize("secondaries", [1, 2])
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc, kernel):
+def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc, kernel, secondaries):
     desc = small_batched()
     sc = eng.Scene(desc)
-    sc.run(want_grad=True, kernel=kernel)
+    sc.run(want_grad=True, kernel=kernel, secondaries=secondaries)
     torch.cuda.synchronize()
     osc = orc.OracleScene(desc)
     for q in (0, 3, 5):
@@ -312,6 +314,28 @@ def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc, kernel
             j1, f1 = stats(g["J"][p], g["J2"][p], n)
             j2, f2 = stats(o["J"][p], o["J2"][p], n)
             assert_totals(j1, f1, j2, f2, rel=1e-2, nsig=5.0)
+
+
+def test_queued_secondaries_over_several_chunks_fp64_match_oracle(eng, orc):
+    """A run longer than one chunk of the secondary queue (2^25 records hold
+    the secondaries of 2^22 histories): chunk after chunk of histories, each
+    followed by the second pass, sums to the oracle's tallies and gradient
+    tallies history for history."""
+    counts = np.array([2_600_000, 2_400_000], dtype=np.int64)
+    desc = W.batched(n_instances=2, precision="f64")
+    desc["instances"]["counts"] = counts
+    sc = eng.Scene(desc)
+    sc.run(want_grad=True, kernel=2, secondaries=2)
+    torch.cuda.synchronize()
+    c = sc.counters()
+    assert c["histories"] == counts.sum() and c["secondaries"] > counts.sum()
+    osc = orc.OracleScene(desc)
+    for q in range(2):
+        o = osc.run(int(counts[q]), inst=q, want_grad=True)
+        g = sc.raw(q)
+        assert np.allclose(g["sum"], o["sum"], rtol=1e-8, atol=1e-10), q
+        assert np.allclose(g["J"], o["J"], rtol=1e-7, atol=1e-8), q
+    sc.close()
 
 
 def test_backward_contracts_gradient_tallies(eng):
