@@ -35,7 +35,7 @@ POWDER_N = 100_000_000
 # ncu smsp__thread_inst_executed.sum / histories on a small case of each
 # workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
 # the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4243, "guide": 2213, "imaging": 3679, "slab": 5818, "batched": 13316,
+INST_PER_HISTORY = {"powder": 4243, "guide": 2213, "imaging": 4002, "slab": 5818, "batched": 13316,
                     "chopper": 1879, "total_scattering": 3478}
 # DRAM bytes of one full-size launch of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
@@ -164,7 +164,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     sc = Scene(desc)
     bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
     runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
-                                   graph=True, first=first)) if grad else None
+                                   graph=True, first=first, secondaries=args.secondaries)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     first = rank * n   # disjoint history ids per rank: weak scaling
@@ -423,6 +423,8 @@ def main() -> None:
     ap.add_argument("--workload", default="powder")
     ap.add_argument("--histories", type=int, default=0, help="override the histories per step")
     ap.add_argument("--kernel", type=int, default=0, help="0 autotuned, 1 history-based, 2 event-based, 3 warp pools")
+    ap.add_argument("--secondaries", type=int, default=0,
+                    help="gradient runs: 0 autotuned, 1 in place, 2 queued for a second pass")
     ap.add_argument("--ctas-per-sm", type=int, default=0,
                     help="CTAs per SM with --kernel (4 x 256 threads selects the 64-register build)")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
