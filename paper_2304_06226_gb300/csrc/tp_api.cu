@@ -47,6 +47,18 @@ bool finite_all(const double* v, int n) {
 
 constexpr double kBoltzmann_meV = 0.08617333;   // k_B in meV/K
 
+// Instance parameters [n][kMaxPar] in the transport precision (what the kernels read).
+std::vector<uint8_t> params_bytes(const std::vector<double>& p, int precision) {
+  std::vector<uint8_t> out(p.size() * (precision == TP_FP64 ? sizeof(double) : sizeof(float)));
+  if (precision == TP_FP64) {
+    std::memcpy(out.data(), p.data(), out.size());
+  } else {
+    float* f = reinterpret_cast<float*>(out.data());
+    for (size_t i = 0; i < p.size(); ++i) f[i] = (float)p[i];
+  }
+  return out;
+}
+
 // Source checks shared by both ways of describing a scene.
 bool source_ok(const tp_source& src) {
   if (src.kind < TP_SRC_PENCIL || src.kind > TP_SRC_MODERATOR) return false;
@@ -117,7 +129,7 @@ struct tp_scene {
   std::vector<double> n_done;  // histories run per instance
   // per-run work description
   unsigned long long *d_prefix = nullptr, *d_first = nullptr, *h_stage = nullptr;
-  double* d_params = nullptr;
+  void* d_params = nullptr;   // instance parameters in the transport precision
   double* d_aux = nullptr;  // backward: [n_inst][n_par] scale + [n_inst] n_done
   double* h_aux = nullptr;
   unsigned long long* d_work = nullptr;
@@ -588,7 +600,7 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.n_inst = s->n_inst;
   k.inst_prefix = s->d_prefix;
   k.inst_first = s->d_first;
-  k.inst_params = s->d_params;
+  k.inst_params = static_cast<const R*>(s->d_params);
   k.work_counter = s->d_work;
   k.sum = s->d_sum; k.sumsq = s->d_sumsq; k.J = s->d_J; k.J2 = s->d_J2;
   k.total_bins = s->total_bins;
@@ -1006,7 +1018,8 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
     return bail(fail(TP_ERR_OOM, "pinned staging buffers"));
   if (cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(TP_ERR_CUDA, "event"));
-  if (cudaMemcpy(s->d_params, s->inst_params.data(), s->inst_params.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+  const std::vector<uint8_t> pb = params_bytes(s->inst_params, s->precision);
+  if (cudaMemcpy(s->d_params, pb.data(), pb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(TP_ERR_CUDA, "upload instance parameters"));
   s->n_done.assign(s->n_inst, 0.0);
   st = tp_reset_tallies(s);
@@ -1081,7 +1094,8 @@ tp_status tp_set_params(tp_scene* s, const double* inst_params) {
     return st;
   }
   TP_CUDA(cudaDeviceSynchronize());
-  TP_CUDA(cudaMemcpy(s->d_params, s->inst_params.data(), s->inst_params.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const std::vector<uint8_t> pb = params_bytes(s->inst_params, s->precision);
+  TP_CUDA(cudaMemcpy(s->d_params, pb.data(), pb.size(), cudaMemcpyHostToDevice));
   s->blob_dirty = true;   // bounding radii and neighbour lists depend on the radii
   return TP_OK;
 }
@@ -1380,7 +1394,7 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   s.d_blob = base;
   s.d_prefix = reinterpret_cast<unsigned long long*>(base + kNaWorkOff);
   s.d_first = s.d_prefix + (s.n_inst + 1);
-  s.d_params = reinterpret_cast<double*>(s.d_first + s.n_inst);
+  s.d_params = s.d_first + s.n_inst;
   s.d_work = reinterpret_cast<unsigned long long*>(base + kNaCtlOff);
   s.d_counters = s.d_work + 1;
   s.d_status = reinterpret_cast<int*>(s.d_counters + kNumCounters);
@@ -1391,7 +1405,8 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   TP_CUDA(cudaMemsetAsync(base + kNaCtlOff, 0, kNaCtlBytes, strm));
   TP_CUDA(cudaMemcpyAsync(s.d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, strm));
   TP_CUDA(cudaMemcpyAsync(s.d_prefix, work.data(), work.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, strm));
-  TP_CUDA(cudaMemcpyAsync(s.d_params, s.inst_params.data(), s.inst_params.size() * sizeof(double), cudaMemcpyHostToDevice, strm));
+  const std::vector<uint8_t> pb = params_bytes(s.inst_params, s.precision);
+  TP_CUDA(cudaMemcpyAsync(s.d_params, pb.data(), pb.size(), cudaMemcpyHostToDevice, strm));
   if (total > 0) {
     int dev = 0, sms = 0;
     TP_CUDA(cudaGetDevice(&dev));

@@ -108,7 +108,7 @@ struct KParams {
   int n_inst;
   const unsigned long long* inst_prefix;  // [n_inst + 1], device
   const unsigned long long* inst_first;   // [n_inst], device: first history id
-  const double* inst_params;              // [n_inst][kMaxPar], device
+  const R* inst_params;                   // [n_inst][kMaxPar], device, transport precision
   unsigned long long total;
   unsigned long long* work_counter;
   int chunk;  // histories a warp claims at once

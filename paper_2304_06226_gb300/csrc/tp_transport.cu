@@ -478,26 +478,29 @@ __device__ __forceinline__ R mirror_R(const DMirror<R>& m, R Q) {
 // ---------------------------------------------------------------------------
 // Scoring: warp-aggregated FP64 atomics
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void agg_add2(double* a, double* b, unsigned long long idx, double v, double v2) {
+template <typename R>
+__device__ __forceinline__ void agg_add2(double* a, double* b, unsigned long long idx, R v, R v2) {
   const unsigned am = __activemask();
   const unsigned grp = __match_any_sync(am, idx);
   const int lane = threadIdx.x & 31;
   if (__any_sync(am, __popc(grp) > 1)) {
-    double s = 0.0, s2 = 0.0;
+    // lanes on the same bin pre-sum in the transport precision (the FP64
+    // pipe is a small fraction of the FP32 one); the tally adds in FP64
+    R s = R(0), s2 = R(0);
     unsigned m = am;
     while (m) {
       const int src = __ffs(m) - 1;
       m &= m - 1;
-      const double x = __shfl_sync(am, v, src);
-      const double y = __shfl_sync(am, v2, src);
+      const R x = __shfl_sync(am, v, src);
+      const R y = __shfl_sync(am, v2, src);
       if ((grp >> src) & 1u) { s += x; s2 += y; }
     }
     v = s;
     v2 = s2;
   }
   if (lane == __ffs(grp) - 1) {
-    atomicAdd(a + idx, v);
-    atomicAdd(b + idx, v2);
+    atomicAdd(a + idx, (double)v);
+    atomicAdd(b + idx, (double)v2);
   }
 }
 
@@ -561,7 +564,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     const int b = tally_bin(T, x0, x1, x2, lam, nscat, path);
     if (b < 0) continue;
     const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
-    const double w = (double)w_;
+    const R w = w_;
     const unsigned long long stride = (unsigned long long)kp.n_inst * kp.total_bins;
     if (!secondary) {
       agg_add2(kp.sum, kp.sumsq, idx, w, w * w);
@@ -569,7 +572,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
 #pragma unroll
         for (int p = 0; p < kMaxPar; ++p) {
           if (p >= kp.npar) break;
-          const double g = w * (double)A[p];
+          const R g = w * A[p];
           agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
         }
       }
@@ -1199,7 +1202,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
       if (((idle >> lane) & 1u) && rank < avail && kp.sec_mode == 2) {
         P = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[chunk_next + rank];   // a queued secondary
 #pragma unroll
-        for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)kp.inst_params[(size_t)P.inst * kMaxPar + i];
+        for (int i = 0; i < kMaxPar; ++i) ip[i] = __ldg(kp.inst_params + (size_t)P.inst * kMaxPar + i);
         dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
         alive = true;
       } else if (((idle >> lane) & 1u) && rank < avail) {
@@ -1213,7 +1216,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
         P.inst = (uint32_t)lo;
         P.hid = (uint32_t)(kp.inst_first[lo] + (g - kp.inst_prefix[lo]));
 #pragma unroll
-        for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)kp.inst_params[(size_t)lo * kMaxPar + i];
+        for (int i = 0; i < kMaxPar; ++i) ip[i] = __ldg(kp.inst_params + (size_t)lo * kMaxPar + i);
         dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
         cnt[C_HIST]++;
         int end = -1;
@@ -1278,9 +1281,9 @@ __device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pr
 
 template <typename R>
 __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst, R (&ip)[kMaxPar], R* dR) {
-  const double* q = kp.inst_params + (size_t)inst * kMaxPar;
+  const R* q = kp.inst_params + (size_t)inst * kMaxPar;
 #pragma unroll
-  for (int i = 0; i < kMaxPar; ++i) ip[i] = (R)__ldg(q + i);
+  for (int i = 0; i < kMaxPar; ++i) ip[i] = __ldg(q + i);
   *dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
 }
 
