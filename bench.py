@@ -35,11 +35,15 @@ POWDER_N = 100_000_000
 # ncu smsp__thread_inst_executed.sum / histories on a small case of each
 # workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
 # the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4243, "guide": 2213, "imaging": 4002, "slab": 5818, "batched": 13316,
-                    "chopper": 1879, "total_scattering": 3478}
-# DRAM bytes of one full-size launch of the kernel variant the autotuner picks
-# (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, variant).
-TRAFFIC_PER_LAUNCH = {("powder", 3): 164352 + 24178176, ("batched", 2): 59709440 + 28421376}
+INST_PER_HISTORY = {"powder": 4264, "guide": 2273, "imaging": 3996, "slab": 5902, "batched": 13076,
+                    "chopper": 1766, "total_scattering": 3385}
+# DRAM bytes of one full-size step of the kernel variant the autotuner picks
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload,
+# variant): powder, one launch of the 64-register warp-pool kernel; batched,
+# the two passes of a queued-secondaries run (measured on 4e7 histories of the
+# same instance mix and scaled by histories: the queue traffic grows with them).
+TRAFFIC_PER_LAUNCH = {("powder", 3): 769792 + 31387904,
+                      ("batched", 2): int((113964544 + 11165827584 + 11703970304 + 134974976) * 591711879 / 4e7)}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
