@@ -273,7 +273,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "tally": {"figure_tally": ft, "mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
                   "counters": counters},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+        # transport launches of each timed step (+ the backward kernel of gradient runs)
+        "gpu_launches": args.steps * (sc.launch_count() + (1 if grad else 0)),
         "clocks": clocks,
     }
     if batched:
@@ -325,6 +326,7 @@ def run_batched(args, W, Scene, torch) -> dict:
     rel = math.sqrt(max(raw["sumsq"].sum() / N - m * m, 0.0) / (N - 1)) / m
     hist_s = total * steps / t
     launch = dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch()))
+    launches_per_step = sc.launch_count() + 1   # transport passes + backward
     fw_s = sum(fw_ms) / 1e3
     achieved = INST_PER_HISTORY["batched"] * total * steps / fw_s
     peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
@@ -336,6 +338,7 @@ def run_batched(args, W, Scene, torch) -> dict:
                          "per_unit": INST_PER_HISTORY["batched"],
                          "kernel": "transport forward with score-function accumulators"},
             "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
+            "gpu_launches_per_step": launches_per_step,
             "rel_stderr_total_median_instance": rel,
             "s_to_eps_per_instance": (rel / 1e-3) ** 2 * N / (hist_s / len(counts)),
             **({"cpu_baseline": cpu_baseline(args, desc, total, grad=True)} if args.cpu_baseline else {})}
@@ -366,10 +369,15 @@ def cpu_baseline(args, desc, n_full, grad: bool = False) -> dict:
     t0 = time.perf_counter()
     done = run(pilot)
     rate = done / (time.perf_counter() - t0)
-    sample = int(min(max(rate * args.cpu_seconds, pilot), args.cpu_sample, n_full))
-    t0 = time.perf_counter()
-    sample = run(sample)
-    dt = time.perf_counter() - t0
+    limit = min(args.cpu_sample, n_full)
+    sample = int(min(max(rate * args.cpu_seconds, pilot), limit))
+    for _ in range(3):   # the pilot's rate is rough: grow the sample until it takes about the target time
+        t0 = time.perf_counter()
+        sample = run(sample)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * args.cpu_seconds or sample >= limit:
+            break
+        sample = int(min(sample * args.cpu_seconds / max(dt, 1e-3), limit))
     what = (f"{sample} histories of the {n_full}-history workload, a share of every instance in proportion "
             f"to its count, with gradients" if grad else f"the first {sample} histories of the {n_full}-history workload")
     return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",

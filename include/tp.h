@@ -322,6 +322,11 @@ tp_status tp_get_counters(tp_scene* s, int64_t out[8]);
  * CTAs per SM. */
 tp_status tp_get_launch(tp_scene* s, int* kernel, int* block_size, int* ctas_per_sm);
 
+/* Transport kernels the last tp_run_histories launched: 1, or with queued
+ * secondaries two per chunk of histories (first pass, second pass); 0 before
+ * any run or if the run had no histories.  No device work. */
+int tp_get_launch_count(const tp_scene* s);
+
 /* Total bins over all tallies (per instance). */
 int tp_total_bins(const tp_scene* s);
 

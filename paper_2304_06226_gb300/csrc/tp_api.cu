@@ -139,6 +139,7 @@ struct tp_scene {
   bool stage_pending = false;
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
+  int launches = 0;   // transport kernels of the last run
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
   int tuned_defer = 0;   // gradient runs: secondaries queued for a second pass
   // queue of radius-derivative secondaries for the second pass (gradient runs)
@@ -1193,6 +1194,12 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   s->kernel = cfg.kernel;
   s->block = cfg.block;
   s->ctas_per_sm = cfg.ctas;
+  if (grad && cfg.defer) {
+    const unsigned long long chunk = std::max(1ull, s->sec_cap / kSecPerHistory);
+    s->launches = (int)(2 * ((total + chunk - 1) / chunk));
+  } else {
+    s->launches = 1;
+  }
   return TP_OK;
 }
 
@@ -1285,6 +1292,8 @@ tp_status tp_get_counters(tp_scene* s, int64_t out[8]) {
   if (status != 0) return fail((tp_status)status, "a device-side wait gave up (status %d)", status);
   return TP_OK;
 }
+
+int tp_get_launch_count(const tp_scene* s) { return s ? s->launches : 0; }
 
 tp_status tp_get_launch(tp_scene* s, int* kernel, int* block, int* ctas) {
   if (!s || !kernel || !block || !ctas) return fail(TP_ERR_INVALID_ARG, "null argument");

@@ -206,6 +206,10 @@ class Scene:
         """(kernel, block size, CTAs per SM) of the last run."""
         return N.tp_get_launch(self.handle)
 
+    def launch_count(self) -> int:
+        """Transport kernels the last run launched (two per chunk with queued secondaries)."""
+        return N.tp_get_launch_count(self.handle)
+
     def means(self) -> torch.Tensor:
         """Per-instance means of every bin, [n_inst, total_bins] float64 on the GPU."""
         out = torch.empty(self.n_inst, self.total_bins, dtype=torch.float64, device="cuda")

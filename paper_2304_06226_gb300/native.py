@@ -113,6 +113,7 @@ SIGNATURES = {
     "tp_get_counters": (C.c_int, [SCENE_P, C.POINTER(C.c_int64)]),
     "tp_get_launch": (C.c_int, [SCENE_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tp_total_bins": (C.c_int, [SCENE_P]),
+    "tp_get_launch_count": (C.c_int, [SCENE_P]),
     "tp_destroy_scene": (None, [SCENE_P]),
     "tp_last_error": (C.c_char_p, []),
     "tp_run_histories_noalloc": (C.c_int, [C.POINTER(tp_scene_desc), C.POINTER(tp_material), C.c_int,
@@ -206,6 +207,10 @@ def tp_get_launch(scene: int) -> tuple[int, int, int]:
     k, b, c = C.c_int(), C.c_int(), C.c_int()
     check(lib.tp_get_launch(scene, C.byref(k), C.byref(b), C.byref(c)), "tp_get_launch")
     return k.value, b.value, c.value
+
+
+def tp_get_launch_count(scene: int) -> int:
+    return lib.tp_get_launch_count(scene)
 
 
 def tp_total_bins(scene: int) -> int:

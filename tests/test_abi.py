@@ -99,6 +99,7 @@ def test_null_arguments(native):
     assert N.lib.tp_set_materials(None, None, 0) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_read_tallies(None, 0, 0, None, None, 0) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_total_bins(None) == 0
+    assert N.lib.tp_get_launch_count(None) == 0
 
 
 def test_invalid_choppers_rejected_before_device_work(native):

@@ -329,6 +329,7 @@ def test_queued_secondaries_over_several_chunks_fp64_match_oracle(eng, orc):
     torch.cuda.synchronize()
     c = sc.counters()
     assert c["histories"] == counts.sum() and c["secondaries"] > counts.sum()
+    assert sc.launch_count() == 4   # two chunks, two passes each
     osc = orc.OracleScene(desc)
     for q in range(2):
         o = osc.run(int(counts[q]), inst=q, want_grad=True)
