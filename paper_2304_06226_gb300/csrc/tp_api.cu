@@ -86,7 +86,7 @@ struct Mat {
 struct LaunchCfg {
   int kernel, block, ctas;
   int stage;   // copy the scene tables into shared memory
-  int hi;      // the 64-register build (plain FP32 runs only)
+  int hi;      // the 64-register build (FP32 runs only)
   int defer;   // gradient runs: secondaries queued and transported in a second pass
   int variant() const { return kernel | (hi ? kVariantHighOcc : 0); }
 };
@@ -646,8 +646,8 @@ tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_cta
   const int b = req_block > 0 ? req_block : 256;
   if (b % 32 != 0 || b < 32 || b > 256)
     return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
-  const bool can_hi = !grad && s->precision == TP_FP32;
-  if (hi > 0 && !can_hi) return fail(TP_ERR_INVALID_ARG, "the 64-register build serves plain FP32 runs only");
+  const bool can_hi = s->precision == TP_FP32;
+  if (hi > 0 && !can_hi) return fail(TP_ERR_INVALID_ARG, "the 64-register build serves FP32 runs only");
   int h = hi > 0 ? 1 : 0, occ = 0;
   const size_t sm = smem_variant(s, kernel, grad, b, stage);
   TP_CUDA(occupancy_transport(kernel | (h ? kVariantHighOcc : 0), s->precision, grad, s->grid_cells > 0, b, sm, &occ));
@@ -767,7 +767,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
             grad ? scratch + (2 + s->n_par) * nb : nullptr, cnt};
   const int cand[][2] = {{TP_KERNEL_EVENT, 256}, {TP_KERNEL_EVENT, 128}, {TP_KERNEL_HISTORY, 128},
                          {TP_KERNEL_HISTORY, 256}, {TP_KERNEL_WARPQ, 256}, {TP_KERNEL_WARPQ, 128}};
-  const int nhi = !grad && s->precision == TP_FP32 ? 2 : 1;   // both register builds
+  const int nhi = s->precision == TP_FP32 ? 2 : 1;   // both register builds
   const int nstage = s->blob_bytes > kStageChoiceBytes && s->blob_bytes <= kMaxStagedBlob ? 2 : 1;
   std::vector<LaunchCfg> cfgs;
   for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]) * nstage * nhi; ++ci) {

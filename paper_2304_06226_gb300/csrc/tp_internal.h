@@ -134,8 +134,8 @@ struct KParams {
 };
 
 // Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ,
-// optionally with kVariantHighOcc: the 64-register build of a plain FP32
-// kernel (4 blocks of 256 threads per SM instead of 3).
+// optionally with kVariantHighOcc: the 64-register build of an FP32 kernel
+// (4 blocks of 256 threads per SM instead of 3).
 constexpr int kVariantHighOcc = 16;
 cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);

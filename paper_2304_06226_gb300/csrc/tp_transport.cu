@@ -1729,9 +1729,9 @@ __global__ void k_backward(const double* __restrict__ J, const double* __restric
 }
 
 // Each kernel exists in two register budgets: 80 registers (3 blocks of 256
-// threads per SM) and, for plain FP32 runs, 64 registers (4 blocks; more warps
-// to hide latency, a few more spills).  The flag kVariantHighOcc on the variant
-// selects the second; gradient and FP64 runs always take the first.
+// threads per SM) and, for FP32 runs, 64 registers (4 blocks; more warps to
+// hide latency, more spills).  The flag kVariantHighOcc on the variant selects
+// the second; FP64 runs always take the first.
 #define TP_KERNEL_TABLE(NAME)                                                                   \
   template <typename R, bool GRAD, bool GRID, int MINB>                                        \
   struct NAME##_t {                                                                            \
@@ -1751,12 +1751,13 @@ template <typename R> struct WqTag { template <bool G, bool D, int M> using k = 
 // Calls F::template run<K>() with K the kernel of (variant, gradients, grid, budget).
 template <typename R, typename F>
 auto with_kernel(int variant, bool grad, bool grid, F&& f) {
-  const bool hi = (variant & kVariantHighOcc) && !grad && sizeof(R) == 4;
+  const bool hi = (variant & kVariantHighOcc) && sizeof(R) == 4;
   const int v = variant & ~kVariantHighOcc;
   auto pick = [&](auto tag) {
     using T = decltype(tag);
-    if (grad) return grid ? f(typename T::template k<true, true, 3>()) : f(typename T::template k<true, false, 3>());
+    if (grad && !hi) return grid ? f(typename T::template k<true, true, 3>()) : f(typename T::template k<true, false, 3>());
     if constexpr (sizeof(R) == 4) {
+      if (grad) return grid ? f(typename T::template k<true, true, 4>()) : f(typename T::template k<true, false, 4>());
       if (hi) return grid ? f(typename T::template k<false, true, 4>()) : f(typename T::template k<false, false, 4>());
     }
     return grid ? f(typename T::template k<false, true, 3>()) : f(typename T::template k<false, false, 3>());
