@@ -43,7 +43,7 @@ INST_PER_HISTORY = {"powder": 4264, "guide": 2273, "imaging": 3996, "slab": 5902
 # the two passes of a queued-secondaries run (measured on 4e7 histories of the
 # same instance mix and scaled by histories: the queue traffic grows with them).
 TRAFFIC_PER_LAUNCH = {("powder", 3): 769792 + 31387904,
-                      ("batched", 2): int((113964544 + 11165827584 + 11703970304 + 134974976) * 591711879 / 4e7)}
+                      ("batched", 2): int((174452480 + 11512364032 + 11701826048 + 134533376) * 591711879 / 4e7)}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
