@@ -242,7 +242,12 @@ typedef struct {
  *   warp; each step runs the event type most of them wait for), or 0: the
  *   autotuner times the variants (and block sizes) on the scene's first run
  *   with and without gradients and keeps the fastest.
- * block_size / ctas_per_sm: 0 = autotuned / the most that fit on an SM.
+ * block_size / ctas_per_sm: 0 = autotuned / the most that fit on an SM.  The
+ *   FP32 kernels exist in an 80-register and a 64-register build; a request
+ *   for more CTAs per SM than the 80-register build allows (more than 3 of 256
+ *   threads) selects the 64-register one.  kernel 0 lets the autotuner pick
+ *   the variant, block size, build and table staging on the scene's first run
+ *   (with and without gradients separately).
  * use_graph: 1 = run as a CUDA graph [work-description copies, work-counter
  *   reset, persistent kernel] captured on the first call with a given launch
  *   (kernel, block, CTAs, gradients, seed, total histories, records) and
