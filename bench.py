@@ -355,13 +355,13 @@ def cpu_baseline(args, desc, n_full, grad: bool = False) -> dict:
     sc = OracleScene(desc)
     counts = np.asarray(desc["instances"]["counts"], dtype=np.float64)
 
-    def run(total):
+    def run(total, threads=cores):
         if not grad:
-            sc.run(total, threads=cores)
+            sc.run(total, threads=threads)
             return total
         share = np.maximum(1, np.rint(total * counts / counts.sum())).astype(np.int64)
         for q, m in enumerate(share):
-            sc.run(int(m), inst=q, threads=cores, want_grad=True)
+            sc.run(int(m), inst=q, threads=threads, want_grad=True)
         return int(share.sum())
 
     pilot = max(10_000, min(args.cpu_sample // 40, 1_000_000))
@@ -380,8 +380,14 @@ def cpu_baseline(args, desc, n_full, grad: bool = False) -> dict:
         sample = int(min(sample * args.cpu_seconds / max(dt, 1e-3), limit))
     what = (f"{sample} histories of the {n_full}-history workload, a share of every instance in proportion "
             f"to its count, with gradients" if grad else f"the first {sample} histories of the {n_full}-history workload")
+    # and on one thread, about a quarter of the target time
+    one = max(1000, int(sample / dt / cores * args.cpu_seconds / 4))
+    t0 = time.perf_counter()
+    one = run(one, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{what}; FP64, {cores} threads", "seconds": dt}
+            "sample": f"{what}; FP64, {cores} threads", "seconds": dt,
+            "single_thread": {"value": one / dt1, "unit": UNIT, "histories": one, "seconds": dt1}}
 
 
 def run_reference(args, rank: int) -> dict | None:
