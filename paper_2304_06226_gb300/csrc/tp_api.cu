@@ -140,6 +140,7 @@ struct tp_scene {
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
   int launches = 0;   // transport kernels of the last run
+  int smem_optin = 0; // shared memory a block may use on this device (queried once)
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
   int tuned_defer = 0;   // gradient runs: secondaries queued for a second pass
   // queue of radius-derivative secondaries for the second pass (gradient runs)
@@ -641,11 +642,21 @@ constexpr uint32_t kStageChoiceBytes = 16 * 1024;
 // than it allows and the 64-register build allows more; 0 / 1 = that build.
 tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_ctas, LaunchCfg* c, int stage = -1,
                   int hi = -1) {
-  if (stage < 0) stage = s->blob_bytes <= kMaxStagedBlob ? 1 : 0;
-  if (stage && s->blob_bytes > kMaxStagedBlob) return fail(TP_ERR_INVALID_ARG, "tables too large to stage");
   const int b = req_block > 0 ? req_block : 256;
   if (b % 32 != 0 || b < 32 || b > 256)
     return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d: need a multiple of 32 in [32, 256]", kernel, b);
+  if (s->smem_optin == 0) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    TP_CUDA(cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  const size_t limit = (size_t)s->smem_optin;
+  // stage the tables when they are small enough and fit beside the neutron bank
+  if (stage < 0) stage = s->blob_bytes <= kMaxStagedBlob && smem_variant(s, kernel, grad, b, 1) <= limit ? 1 : 0;
+  if (stage && s->blob_bytes > kMaxStagedBlob) return fail(TP_ERR_INVALID_ARG, "tables too large to stage");
+  if (smem_variant(s, kernel, grad, b, stage) > limit)
+    return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d needs %zu bytes of shared memory; a block may use %zu",
+                kernel, b, smem_variant(s, kernel, grad, b, stage), limit);
   const bool can_hi = s->precision == TP_FP32;
   if (hi > 0 && !can_hi) return fail(TP_ERR_INVALID_ARG, "the 64-register build serves FP32 runs only");
   int h = hi > 0 ? 1 : 0, occ = 0;

@@ -661,3 +661,20 @@ def test_plain_workloads_full_size_in_bench_launch_shape(eng, orc, name):
     m1, e1 = stats(gpu["raw"]["sum"], gpu["raw"]["sumsq"], n)
     m2, e2 = stats(ob["sum"], ob["sumsq"], ns)
     assert_totals(m1, e1, m2, e2)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_imaging_density_gradients_fp64_match_oracle_history_by_history(eng, orc, kernel):
+    """The 1000-primitive scene with the three density gradients (no radius
+    parameter: the event kernel runs its single-phase loop), FP64, against
+    the brute-force oracle: tallies and gradient tallies."""
+    n = 4000
+    desc = W.imaging(n_histories=n, precision="f64", psd_bins=32)
+    sc = eng.Scene(desc)
+    sc.run(n, want_grad=True, kernel=kernel)
+    torch.cuda.synchronize()
+    g = sc.raw(0)
+    o = orc.OracleScene(desc).run(n, want_grad=True)
+    assert np.allclose(g["sum"], o["sum"], rtol=1e-8, atol=1e-12)
+    assert np.allclose(g["J"], o["J"], rtol=1e-7, atol=1e-10)
+    sc.close()
