@@ -1,9 +1,13 @@
 // tp_transport.cu -- sm_103a kernels of the biased neutron history loop.
 //
-// One persistent launch processes every history of every instance.  Each warp
-// claims chunks of history ids with one global atomic, and each lane carries
-// one neutron in registers: a lane whose neutron ends takes the next id of its
-// warp's chunk at the top of the next step, so lanes stay busy until the work
+// One persistent launch processes every history of every instance (gradient
+// runs may add a second launch over the queued radius-derivative secondaries).
+// Three kernels share the physics and differ in how neutrons meet lanes: the
+// history kernel (each lane carries one neutron in registers and takes the next
+// id of its warp's chunk when it ends), the event kernel (a block-wide bank of
+// neutrons sorted every iteration by what they wait for) and the warp-pool
+// kernel (each warp runs the most common pending event of its own pool); all
+// claim history ids with global atomics, so lanes stay busy until the work
 // runs out (no per-history kernel, no host round trip).  A step is one event of
 // the simulation flow of §3.1: cross sections of the current volume, biased
 // flight length (§2.4, Eq. eStepLength2), distance to the next boundary, move
@@ -20,7 +24,8 @@
 //
 // Tallies are FP64 sums of w and w^2 per bin (plus the score-function tallies),
 // added with warp-aggregated atomics: lanes hitting the same bin combine their
-// values with shuffles and one lane issues the atomic.
+// values with shuffles (in the transport precision) and one lane issues the
+// FP64 atomic.
 #include <cuda_runtime.h>
 
 #include <cfloat>
