@@ -23,9 +23,10 @@
  *                            implicit capture, biased-vs-unbiased equality)
  *   isotropic scattering     pinned (angular moments, infinite-medium closed forms)
  *   powder Bragg sigma       pinned in its lambda and line dependence against a
- *                            reflection-by-reflection enumeration; the absolute
- *                            prefactor lambda^2/(2 V0^2) is a reading of the
- *                            textbook powder average and is otherwise unpinned
+ *                            reflection-by-reflection enumeration, and in its
+ *                            absolute prefactor lambda^2/(2 V0^2) against the
+ *                            kinematic single-crystal cross section averaged by
+ *                            Monte Carlo over random crystal orientations
  *   mirror R(Q), reflection  pinned (Table tableMirror values, bounce-count closed form)
  *   score-function gradients pinned (closed-form uncollided derivatives, finite
  *                            differences on common random numbers)

@@ -319,3 +319,37 @@ def test_radius_gradient_of_uncollided_cylinder_transmission(oracle_mod, threads
                             -math.pi / 2, math.pi / 2)[0] / (2 * b)
     gm, ge = stats(r["J"][0], r["J2"][0], n)
     assert abs(gm[0] - dT_ref) < 4 * ge[0], (gm[0], ge[0], dT_ref)
+
+
+@pytest.mark.parametrize("lam", [1.5, 2.5])
+def test_powder_bragg_prefactor_from_orientation_averaged_single_crystal(lam):
+    """The absolute powder Bragg cross section of the oracle (the powder
+    average of Eq. eCohEla) against an independent route: the kinematic
+    single-crystal cross section of one reflection, lambda^3 |F|^2 /
+    (V0 sin 2theta_B) times a narrow rocking profile (Gaussian, width eta) in
+    the glancing angle, averaged by Monte Carlo over uniformly random crystal
+    orientations (random lattice-plane normals on the sphere).  Summed over
+    the reflections (a +-G pair reflects at most once per orientation) and
+    divided by V0, it must give the oracle's Sigma_Bragg(lambda)."""
+    from oracle import oracle as O
+    O.build()
+    desc = W.powder(n_histories=1)
+    lines = W.fcc_bragg_lines()
+    d = np.asarray(lines["d"]); m = np.asarray(lines["mult"]); F2 = np.asarray(lines["F2"]); V0 = lines["V0"]
+    rng = np.random.default_rng(2024)
+    n = rng.normal(size=(8_000_000, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    theta = np.arcsin(np.abs(n[:, 2]))          # glancing angle of a beam along z on the planes
+    eta = 0.003
+    sigma_cell = 0.0                             # barn per unit cell
+    for di, mi, fi in zip(d, m, F2):
+        s = lam / (2.0 * di)
+        if s >= 1.0:
+            continue                             # no Bragg angle: beyond the edge
+        tb = np.arcsin(s)
+        w = np.exp(-0.5 * ((theta - tb) / eta) ** 2) / (math.sqrt(2 * math.pi) * eta)
+        per_pair = lam ** 3 * fi / (V0 * math.sin(2 * tb)) * w.mean()
+        sigma_cell += 0.5 * mi * per_pair
+    expect = sigma_cell / V0                     # barn / A^3 = 1/cm
+    got = O.OracleScene(desc).sigma(0, lam)[2]
+    assert abs(got - expect) <= 0.01 * expect, (got, expect)
