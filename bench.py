@@ -30,13 +30,35 @@ sys.path.insert(0, str(ROOT))
 METRIC = "histories/s on 1 GB300: plain vs batched+adjoint, at matched tally error"
 UNIT = "histories/s"
 POWDER_N = 100_000_000
-# Algorithmic work per history: thread instructions the history-based kernel
-# (one neutron per thread, no regrouping overhead) executes per history, from
-# ncu smsp__thread_inst_executed.sum / histories on a small case of each
-# workload (profiles/per_unit_instruction_counts.md).  The per-unit figure of
-# the ALU-issue roofline, whichever kernel variant runs.
-INST_PER_HISTORY = {"powder": 4264, "guide": 2273, "imaging": 3996, "slab": 5902, "batched": 13076,
-                    "chopper": 1766, "total_scattering": 3385}
+# Thread instructions the history-based kernel (one neutron per thread, no
+# regrouping overhead) executed per history, from ncu
+# smsp__thread_inst_executed.sum / histories on a small case of each workload:
+# an implementation's count, reported beside the algorithmic one below.
+EXECUTED_INST_PER_HISTORY = {"powder": 4264, "guide": 2273, "imaging": 3996, "slab": 5902, "batched": 13076,
+                             "chopper": 1766, "total_scattering": 3385}
+# Algorithmic lane operations of the method per step type, counted from its
+# formulas (not from any kernel):
+#   every event (biased flight, Eq. eStepLength2, and weight, Eq. eWeight):
+#     one Philox4x32-10 block, 10 rounds x (2 mul-hi + 2 mul-lo + 4 xor + 2 key
+#     adds) = 100; two uniforms 6; cross sections of the volume (1/v
+#     absorption, incoherent, Bragg prefix-sum search over 18 lines, Sigma_t,
+#     Sigma_g) 31; step -ln(xi)/Sigma_g 3; move 4; weight exp 3; distance to
+#     the next boundary 40 (a tube's exit quadratic ~30, a box's three slabs
+#     ~12, plus the world region's bounding-sphere tests) = 187
+#   a collision: process choice and weight division 6, isotropic direction 13
+#     (a Bragg line adds a second Philox block, two searches and a rotation,
+#     ~150, in a minority of collisions) = 40 on average
+#   a boundary crossing: nudge, relocation among neighbours and the scorer's
+#     bin (angle, atomics) = 40
+OPS_PER_EVENT, OPS_PER_COLLISION, OPS_PER_CROSSING = 187, 40, 40
+
+
+def algorithmic_ops_per_history(counters: dict) -> float:
+    h = max(1, counters["histories"])
+    return (OPS_PER_EVENT * counters["events"] + OPS_PER_COLLISION * counters["collisions"]
+            + OPS_PER_CROSSING * counters["crossings"]) / h
+
+
 # DRAM bytes of one full-size step of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload,
 # variant): powder, one launch of the 64-register warp-pool kernel; batched,
@@ -51,9 +73,13 @@ FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, 
 # Workloads whose configuration asks for the adjoint: their step is a run with
 # the score-function accumulators plus the backward contraction.
 GRAD_WORKLOADS = ("batched", "imaging")
-SM_COUNT = 152
-LANES_PER_SM = 128          # FP32/INT32 lanes (4 SMSPs x 32)
-SM_MAX_MHZ = 2070.0
+
+
+def measured_peaks() -> dict:
+    """The device's measured rates (tp_measure_peaks): FP32 FMA, integer,
+    special-function and FP64 lane rates, FP64 atomics, L2 read bandwidth."""
+    from paper_2304_06226_gb300 import native as NN
+    return NN.tp_measure_peaks()
 
 
 def workload_desc(name: str):
@@ -146,6 +172,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     from paper_2304_06226_gb300 import build
     build.build()
     from paper_2304_06226_gb300.engine import Scene
+    from paper_2304_06226_gb300 import shard
     import workloads as W
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -171,18 +198,23 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                                    graph=True, first=first, secondaries=args.secondaries)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-    first = rank * n   # disjoint history ids per rank: weak scaling
+    first = 0
 
-    def step(st=None):
+    def step(k, st=None):
+        # every step and every rank takes its own history ids (weak scaling):
+        # the tallies then hold steps x ranks x n distinct histories
+        nonlocal first
+        first = shard.step_first(k, rank, world, n)
         if grad:
             runs(st)
             sc.backward(bgrad, stream=st)
         else:
             sc.run(n, first=first, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
 
+    peaks = measured_peaks() if rank == 0 else None
     # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
     sc.reset()
     if dist:
@@ -195,7 +227,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         for k in range(args.steps):
             flush_l2(flush)
             ev[k][0].record(stream)
-            step(stream)
+            step(k, stream)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -208,10 +240,14 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     counters = sc.counters()
     tot = n * args.steps
     value = world * tot / dev_s
+    if dist:
+        # one FP64 sum all-reduce of every rank's partial tallies (after the
+        # timed steps): rank 0 then holds the statistics of all histories
+        sc.allreduce(sc.counts * args.steps if grad else [tot])
     # ---- tally error of the integrated detector total (per history) ----
     q = int(np.argsort(sc.counts)[len(sc.counts) // 2]) if grad else 0   # median-count instance
     raw = sc.raw(q)
-    N = float(sc.counts[q] * args.steps) if grad else float(tot)
+    N = float(sc.counts[q] * args.steps * world) if grad else float(tot * world)
     ft = FIGURE_TALLY.get(args.workload, 0)
     lo, hi = sc.tally_off[ft], sc.tally_off[ft + 1]
     mean_tot = raw["sum"][lo:hi].sum() / N
@@ -231,6 +267,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     host_grad = np.empty((sc.n_inst, max(1, sc.n_par)))
     for k in range(e2e_steps):
         sc.reset()
+        first = shard.step_first(args.steps + k, rank, world, n)
         if grad:
             runs()
             g = sc.backward(bgrad)
@@ -248,15 +285,17 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     # ---- batched + adjoint ----
     batched = None
     if args.batched and rank == 0 and not grad:
-        batched = run_batched(args, W, Scene, torch)
+        batched = run_batched(args, W, Scene, torch, peaks)
 
     if rank != 0:
         return None
-    inst_ph = INST_PER_HISTORY.get(args.workload)
+    exec_ph = EXECUTED_INST_PER_HISTORY.get(args.workload)
     traffic = TRAFFIC_PER_LAUNCH.get((args.workload, sc.launch()[0])) if not args.histories else None
     clocks = clk.summary()
-    peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
-    achieved = inst_ph * tot / (sum(kernel_ms) / 1e3) if inst_ph else None
+    peak = peaks["fp32_fma"]
+    alg_ph = algorithmic_ops_per_history(counters)
+    t_s = sum(kernel_ms) / 1e3
+    achieved = alg_ph * tot / t_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
@@ -265,10 +304,19 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "config": workload_config(args.workload, label, {
             "histories_per_step_per_gpu": n, "tallies": "FP64 sum w, sum w^2 per bin",
             "launch": dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch())),
-            "parallelism": f"history ids sharded over {world} GPU(s)"}),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "per_unit": inst_ph, "peak_basis": "152 SMs x 128 lanes x 2070 MHz"},
+            "parallelism": f"history ids sharded over {world} GPU(s), one FP64 all-reduce of the tallies"}),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "per_unit": alg_ph, "per_unit_basis": (
+                         f"algorithmic lane operations per history: {OPS_PER_EVENT} per event + "
+                         f"{OPS_PER_COLLISION} per collision + {OPS_PER_CROSSING} per crossing, "
+                         "weighted by this run's counters"),
+                     "peak_basis": (f"measured FP32 FMA lane rate of this GPU (tp_measure_peaks, "
+                                    f"{peaks['sm_clock_mhz']:.0f} MHz during the measurement)"),
+                     "executed": ({"per_unit": exec_ph, "frac": exec_ph * tot / t_s / peak,
+                                   "basis": "thread instructions per history of the history-based kernel (ncu)"}
+                                  if exec_ph else None)},
+        "peaks": peaks,
         "kernel_ms": kernel_ms,
         "tally": {"figure_tally": ft, "mean_total": mean_tot, "rel_stderr_total": rel_err, "fom": fom_plain,
                   "counters": counters},
@@ -292,7 +340,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     return line
 
 
-def run_batched(args, W, Scene, torch) -> dict:
+def run_batched(args, W, Scene, torch, peaks) -> dict:
     """Workload 4: 256 instances, one persistent launch, gradients + backward."""
     desc = W.batched()
     sc = Scene(desc)
@@ -307,9 +355,11 @@ def run_batched(args, W, Scene, torch) -> dict:
     steps = max(1, args.batched_steps)
     a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     fw_ms, bw_ms = [], []
-    for _ in range(steps):
+    span = int(counts.max())
+    for k in range(steps):
         a.record(stream)
-        sc.run(want_grad=True, stream=stream, graph=True)   # one persistent launch, replayed from a CUDA graph
+        # one CUDA graph per step, replayed with new first ids: each step runs distinct histories
+        sc.run(want_grad=True, stream=stream, graph=True, first=k * span)
         b.record(stream)
         sc.backward(grad, stream=stream)
         c.record(stream)
@@ -328,14 +378,16 @@ def run_batched(args, W, Scene, torch) -> dict:
     launch = dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch()))
     launches_per_step = sc.launch_count() + 1   # transport passes + backward
     fw_s = sum(fw_ms) / 1e3
-    achieved = INST_PER_HISTORY["batched"] * total * steps / fw_s
-    peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    alg_ph = algorithmic_ops_per_history(sc.counters())
+    achieved = alg_ph * total * steps / fw_s
+    peak = peaks["fp32_fma"]
     sc.close()
     return {"value": hist_s, "unit": UNIT, "instances": int(len(counts)), "histories_per_step": total,
             "launch": launch,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-inst/s",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                          "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("batched", launch["kernel"])),
-                         "per_unit": INST_PER_HISTORY["batched"],
+                         "per_unit": alg_ph, "per_unit_basis": "algorithmic lane operations per history "
+                         "(secondaries included), weighted by the run's counters",
                          "kernel": "transport forward with score-function accumulators"},
             "forward_ms": fw_ms, "backward_ms": bw_ms, "gradients": "d tallies / d (radius, scale, density)",
             "gpu_launches_per_step": launches_per_step,
@@ -454,6 +506,9 @@ def main() -> None:
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus != world:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}: launch N ranks with "
+                         f"python -m torch.distributed.run --nproc-per-node N bench.py --gpus N")
     if args.impl == "reference":
         line = run_reference(args, rank)
     else:

@@ -46,7 +46,8 @@ typedef enum {
   TP_ERR_CUDA = 3,        /* a CUDA runtime error */
   TP_ERR_OOM = 4,         /* device allocation failed */
   TP_ERR_TIMEOUT = 5,     /* a device-side wait or iteration cap gave up */
-  TP_ERR_STATE = 6        /* call out of order (e.g. run before tp_set_materials) */
+  TP_ERR_STATE = 6,       /* call out of order (e.g. run before tp_set_materials) */
+  TP_ERR_ABORTED = 7      /* the run was stopped by tp_abort; its tallies are partial */
 } tp_status;
 
 /* Solids (Appendix A: Box, Tube, Orb/Sphere with full phi). */
@@ -281,8 +282,10 @@ enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2, TP_KERNEL
 
 /* Runs histories and accumulates their scores into the scene's tallies
  * (sum w, sum w^2 per bin per instance, and the gradient tallies).  Returns
- * after the launch is queued on the stream; the per-run status (truncation
- * count, lost particles) is available from tp_get_counters. */
+ * after the launch is queued on the stream, so errors raised on the device
+ * (a bounded wait that gave up: TP_ERR_TIMEOUT; a run stopped by tp_abort:
+ * TP_ERR_ABORTED) are reported by the next tp_get_counters, together with the
+ * per-run counts (truncated histories, lost particles). */
 tp_status tp_run_histories(tp_scene* s, const tp_run* r);
 
 /* Mean and standard error per source history of every bin of `tally` for
@@ -298,6 +301,16 @@ tp_status tp_read_tallies(tp_scene* s, int tally, int instance, double* mean, do
  * [n_params][total bins] of sum w A_p and sum (w A_p)^2. */
 tp_status tp_read_raw(tp_scene* s, int instance, double* sum, double* sumsq, double* J, double* J2,
                       int on_device);
+
+/* Overwrites the raw accumulators of one instance -- sum, sumsq
+ * ([total bins]), J, J2 ([n_params][total bins], may be NULL) -- and its
+ * history count, the layout of tp_read_raw.  For combining runs made
+ * elsewhere: after the partial accumulators of several GPUs (disjoint history
+ * ids) are summed, writing the sums back makes tp_read_tallies and
+ * tp_backward give the statistics of all histories (§2.1: the estimate is a
+ * mean over independent histories, so partial sums add).  Synchronises. */
+tp_status tp_write_raw(tp_scene* s, int instance, const double* sum, const double* sumsq, const double* J,
+                       const double* J2, double n_histories, int on_device);
 
 /* Backward pass of the tallies with respect to the instance parameters:
  *   grad_params[i][p] = sum_b grad_tallies[i][b] * dmean_b/dtheta_p
@@ -320,8 +333,29 @@ tp_status tp_reset_tallies(tp_scene* s);
 
 /* Counters since the last reset: histories, events, collisions, boundary
  * crossings, truncated histories, lost neutrons, mirror reflections, derivative
- * secondaries.  Synchronises. */
+ * secondaries.  Synchronises the device, fills `out` in every case, then returns
+ * the status the kernels recorded since the last reset: TP_OK,
+ * TP_ERR_TIMEOUT (a block's bounded wait for its copy of the scene tables gave
+ * up; that block transported nothing) or TP_ERR_ABORTED (tp_abort). */
 tp_status tp_get_counters(tp_scene* s, int64_t out[8]);
+
+/* Asks every run of the scene that is queued or running to stop: the kernels
+ * poll a flag in mapped host memory whenever they claim new histories, claim
+ * none once it is set, finish the neutrons they hold and record
+ * TP_ERR_ABORTED.  Callable from any host thread, also while another thread
+ * waits for the run; it does not wait itself.  The scene stays aborted (later
+ * runs stop at once) until tp_reset_tallies, which clears the flag along with
+ * the partial tallies.  No device call is made. */
+tp_status tp_abort(tp_scene* s);
+
+/* Test hooks, for the failure-detection tests only (0 = normal operation).
+ * TP_TEST_SKIP_TABLE_COPY: the kernels arm their wait for the bulk copy of the
+ * scene tables into shared memory but issue no copy, so that the bounded wait
+ * (about half a second) runs out: each block records TP_ERR_TIMEOUT and
+ * returns with nothing in flight and nothing transported.  s = NULL sets the
+ * flags of tp_run_histories_noalloc, which has no scene. */
+enum { TP_TEST_SKIP_TABLE_COPY = 1 };
+tp_status tp_set_test_flags(tp_scene* s, int flags);
 
 /* Launch configuration of the last run: kernel (TP_KERNEL_*), block size and
  * CTAs per SM. */
@@ -350,10 +384,19 @@ int tp_total_bins(const tp_scene* s);
  * until the process exits.
  *  - desc, mats[n_mats], bias ([n_mats][TP_NPROC], NULL = all 1) and r are
  *    read as in tp_create_scene, tp_set_materials, tp_set_bias and
- *    tp_run_histories; r->want_grad and r->records must be 0/NULL.
+ *    tp_run_histories, with these restrictions (TP_ERR_INVALID_ARG
+ *    otherwise): r->want_grad, r->records, r->use_graph and r->secondaries
+ *    must be 0/NULL, and r->kernel 0 or TP_KERNEL_HISTORY: the call always
+ *    runs the history-based kernel with the tables staged when they fit, and
+ *    builds no uniform grid, so a scene of many primitives tests all of them
+ *    at every step of the world region (same results, more work).
  *  - sum, sumsq: caller-owned device arrays of [n_instances][total bins]
  *    doubles; the call ADDS sum w and sum w^2 of every bin into them.
  *  - counters_out (host, may be NULL): the counters of this call.
+ *  - The call waits for its work and then reads the status word the kernel
+ *    leaves, whether or not counters_out is given: a bounded device wait that
+ *    gave up returns TP_ERR_TIMEOUT (the sums then hold nothing of this
+ *    call).
  *  - Limits: at most TP_NOALLOC_MAX_INSTANCES instances and
  *    TP_NOALLOC_MAX_TABLE_BYTES bytes of scene tables (checked first:
  *    TP_ERR_INVALID_ARG with a message naming the limit).
@@ -370,6 +413,33 @@ int tp_total_bins(const tp_scene* s);
 tp_status tp_run_histories_noalloc(const tp_scene_desc* desc, const tp_material* mats, int n_mats,
                                    const double* bias, const tp_run* r, double* sum, double* sumsq,
                                    int64_t counters_out[8]);
+
+/* ------------------------------------------------------------------------
+ * Measured hardware rates of the current device (no counterpart in the paper:
+ * the denominators of this library's roofline).  The history loop is bound by
+ * instruction issue -- FP32 and integer arithmetic, the special-function unit
+ * for its logarithms, exponentials and sines, FP64 atomics into the tallies --
+ * not by HBM or tensor cores, so its roofline fraction is taken against these
+ * rates, measured by short bounded microbenchmarks (each a fixed number of
+ * iterations of independent dependency chains at full occupancy, timed with
+ * CUDA events on `stream` after a warm-up launch).  Rates are lane operations
+ * per second over the whole device, at whatever clock the device runs
+ * (sm_clock_mhz, measured during the FP32 kernel from clock64 and the global
+ * timer).  Allocates and frees about 35 MB of device scratch; synchronises
+ * `stream`; takes well under a second. */
+typedef struct {
+  double fp32_fma;          /* FP32 fused multiply-adds */
+  double int32_imad;        /* 32-bit integer multiply-adds */
+  double int32_logic;       /* 32-bit three-input logic operations */
+  double mufu_lg2, mufu_ex2, mufu_sin;   /* special-function unit, approximate */
+  double fp64_fma;          /* FP64 fused multiply-adds */
+  double atomic_f64_spread; /* FP64 global atomic adds into 3600 bins (one detector) */
+  double atomic_f64_hot;    /* FP64 global atomic adds piled on 32 bins */
+  double l2_read_bytes;     /* bytes per second read from an L2-resident buffer */
+  double sm_clock_mhz;
+  int sm_count;
+} tp_peaks;
+tp_status tp_measure_peaks(tp_peaks* out, void* stream);
 
 void tp_destroy_scene(tp_scene* s);
 const char* tp_last_error(void);

@@ -19,7 +19,8 @@ OBJDIR = PKG / "_build"
 # precision so that the halves build in parallel
 UNITS = [("tp_transport.cu", "tp_transport_f32.o", ["-DTP_BUILD_F32"]),
          ("tp_transport.cu", "tp_transport_f64.o", ["-DTP_BUILD_F64"]),
-         ("tp_api.cu", "tp_api.o", [])]
+         ("tp_api.cu", "tp_api.o", []),
+         ("tp_peaks.cu", "tp_peaks.o", [])]
 SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -38,6 +39,18 @@ tp_status fail(tp_status s, const char* fmt, ...) {
       return fail(e_ == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA, "%s: %s (%s:%d)", \
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
   } while (0)
+
+// The status word the kernels leave (0 = fine) as a tp_status with a message.
+tp_status device_status(int status) {
+  if (status == 0) return TP_OK;
+  if (status == TP_ERR_TIMEOUT)
+    return fail(TP_ERR_TIMEOUT, "a block's bounded wait for its copy of the scene tables gave up");
+  if (status == TP_ERR_ABORTED) return fail(TP_ERR_ABORTED, "the run was stopped by tp_abort");
+  return fail((tp_status)status, "device status %d", status);
+}
+
+// Test flags of the allocation-free call (tp_set_test_flags with no scene).
+std::atomic<int> g_noalloc_test_flags{0};
 
 bool finite_all(const double* v, int n) {
   for (int i = 0; i < n; ++i)
@@ -135,6 +148,10 @@ struct tp_scene {
   unsigned long long* d_work = nullptr;
   unsigned long long* d_counters = nullptr;
   int* d_status = nullptr;
+  // abort request: host-written flag in mapped pinned memory (tp_abort)
+  volatile int* h_abort = nullptr;
+  int* d_abort = nullptr;
+  int test_flags = 0;   // tp_set_test_flags
   cudaEvent_t stage_done = nullptr;
   bool stage_pending = false;
   // launch configuration: last used, and the autotuned choice per gradient mode
@@ -612,6 +629,8 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.total_bins = s->total_bins;
   k.counters = s->d_counters;
   k.status = s->d_status;
+  k.abort_flag = s->d_abort;
+  k.test_flags = s->test_flags;
 }
 
 size_t smem_bytes(const tp_scene* s) { return s->blob_bytes <= kMaxStagedBlob ? align16(s->blob_bytes) : 0; }
@@ -1034,6 +1053,16 @@ tp_status tp_create_scene(const tp_scene_desc* d, tp_scene** out) {
     return bail(fail(TP_ERR_OOM, "pinned staging buffers"));
   if (cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(TP_ERR_CUDA, "event"));
+  {
+    void* hp = nullptr;
+    void* dp = nullptr;
+    if (cudaHostAlloc(&hp, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+      return bail(fail(TP_ERR_OOM, "mapped abort flag"));
+    s->h_abort = static_cast<volatile int*>(hp);
+    *s->h_abort = 0;
+    if (cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) return bail(fail(TP_ERR_CUDA, "abort flag address"));
+    s->d_abort = static_cast<int*>(dp);
+  }
   const std::vector<uint8_t> pb = params_bytes(s->inst_params, s->precision);
   if (cudaMemcpy(s->d_params, pb.data(), pb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(TP_ERR_CUDA, "upload instance parameters"));
@@ -1118,6 +1147,9 @@ tp_status tp_set_params(tp_scene* s, const double* inst_params) {
 
 tp_status tp_reset_tallies(tp_scene* s) {
   if (!s) return fail(TP_ERR_INVALID_ARG, "null scene");
+  // a run still draining after tp_abort must have stopped before the flag clears
+  TP_CUDA(cudaDeviceSynchronize());
+  if (s->h_abort) *s->h_abort = 0;
   const size_t nb = (size_t)s->n_inst * std::max(1, s->total_bins);
   TP_CUDA(cudaMemset(s->d_sum, 0, nb * sizeof(double)));
   TP_CUDA(cudaMemset(s->d_sumsq, 0, nb * sizeof(double)));
@@ -1151,7 +1183,7 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   unsigned long long total = 0;
   for (int i = 0; i < s->n_inst; ++i) {
     const unsigned long long first = r->first_history ? r->first_history[i] : 0ull;
-    if (r->n_histories[i] > 0xffffffffull || first + r->n_histories[i] > 0x100000000ull)
+    if (r->n_histories[i] > 0xffffffffull || first > 0x100000000ull - r->n_histories[i])
       return fail(TP_ERR_INVALID_ARG, "instance %d: history ids must stay below 2^32", i);
     s->h_stage[i] = total;
     s->h_stage[s->n_inst + 1 + i] = first;
@@ -1255,6 +1287,28 @@ tp_status tp_read_raw(tp_scene* s, int instance, double* sum, double* sumsq, dou
   return TP_OK;
 }
 
+tp_status tp_write_raw(tp_scene* s, int instance, const double* sum, const double* sumsq, const double* J,
+                       const double* J2, double n_histories, int on_device) {
+  g_err.clear();
+  if (!s || !sum || !sumsq) return fail(TP_ERR_INVALID_ARG, "null argument");
+  if (instance < 0 || instance >= s->n_inst) return fail(TP_ERR_INVALID_ARG, "instance %d", instance);
+  if (!(n_histories >= 0) || !std::isfinite(n_histories)) return fail(TP_ERR_INVALID_ARG, "n_histories %g", n_histories);
+  if ((J || J2) && s->n_par == 0) return fail(TP_ERR_INVALID_ARG, "scene has no parameters");
+  const size_t nb = (size_t)s->total_bins;
+  const size_t off = (size_t)instance * nb;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  TP_CUDA(cudaDeviceSynchronize());
+  TP_CUDA(cudaMemcpy(s->d_sum + off, sum, nb * sizeof(double), kind));
+  TP_CUDA(cudaMemcpy(s->d_sumsq + off, sumsq, nb * sizeof(double), kind));
+  for (int p = 0; p < s->n_par; ++p) {
+    const size_t dst = ((size_t)p * s->n_inst + instance) * nb;
+    if (J) TP_CUDA(cudaMemcpy(s->d_J + dst, J + p * nb, nb * sizeof(double), kind));
+    if (J2) TP_CUDA(cudaMemcpy(s->d_J2 + dst, J2 + p * nb, nb * sizeof(double), kind));
+  }
+  s->n_done[instance] = n_histories;
+  return TP_OK;
+}
+
 tp_status tp_backward(tp_scene* s, const double* grad_tallies, double* grad_params, int on_device, void* stream) {
   g_err.clear();
   if (!s || !grad_tallies || !grad_params) return fail(TP_ERR_INVALID_ARG, "null argument");
@@ -1300,7 +1354,24 @@ tp_status tp_get_counters(tp_scene* s, int64_t out[8]) {
   TP_CUDA(cudaMemcpy(h, s->d_counters, sizeof h, cudaMemcpyDeviceToHost));
   TP_CUDA(cudaMemcpy(&status, s->d_status, sizeof status, cudaMemcpyDeviceToHost));
   for (int i = 0; i < kNumCounters; ++i) out[i] = (int64_t)h[i];
-  if (status != 0) return fail((tp_status)status, "a device-side wait gave up (status %d)", status);
+  return device_status(status);
+}
+
+tp_status tp_abort(tp_scene* s) {
+  if (!s || !s->h_abort) return fail(TP_ERR_INVALID_ARG, "null scene");
+  *s->h_abort = 1;
+  return TP_OK;
+}
+
+tp_status tp_set_test_flags(tp_scene* s, int flags) {
+  g_err.clear();
+  if (flags & ~TP_TEST_SKIP_TABLE_COPY) return fail(TP_ERR_INVALID_ARG, "unknown test flags %#x", flags);
+  if (!s) {
+    g_noalloc_test_flags.store(flags);
+    return TP_OK;
+  }
+  s->test_flags = flags;
+  if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }   // the flags are baked into it
   return TP_OK;
 }
 
@@ -1327,6 +1398,7 @@ void tp_destroy_scene(tp_scene* s) {
   cudaFree(s->d_sec); cudaFree(s->d_sec_count);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   if (s->h_aux) cudaFreeHost(s->h_aux);
+  if (s->h_abort) cudaFreeHost(const_cast<int*>(s->h_abort));
   if (s->stage_done) cudaEventDestroy(s->stage_done);
   delete s;
 }
@@ -1383,6 +1455,10 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   if (!d || !r || !r->n_histories || !sum || !sumsq || (n_mats > 0 && !mats) || n_mats < 0)
     return fail(TP_ERR_INVALID_ARG, "null argument");
   if (r->want_grad || r->records) return fail(TP_ERR_INVALID_ARG, "no gradients or records in the allocation-free call");
+  if (r->kernel != TP_KERNEL_AUTO && r->kernel != TP_KERNEL_HISTORY)
+    return fail(TP_ERR_INVALID_ARG, "kernel %d: the allocation-free call runs the history kernel only", r->kernel);
+  if (r->use_graph || r->secondaries)
+    return fail(TP_ERR_INVALID_ARG, "the allocation-free call takes no graph or secondaries option");
   if (d->n_instances < 1 || d->n_instances > TP_NOALLOC_MAX_INSTANCES)
     return fail(TP_ERR_INVALID_ARG, "n_instances %d: the allocation-free call takes 1..%d", d->n_instances,
                 TP_NOALLOC_MAX_INSTANCES);
@@ -1404,7 +1480,7 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   std::vector<unsigned long long> work((size_t)2 * s.n_inst + 1);
   for (int i = 0; i < s.n_inst; ++i) {
     const unsigned long long first = r->first_history ? r->first_history[i] : 0ull;
-    if (r->n_histories[i] > 0xffffffffull || first + r->n_histories[i] > 0x100000000ull)
+    if (r->n_histories[i] > 0xffffffffull || first > 0x100000000ull - r->n_histories[i])
       return fail(TP_ERR_INVALID_ARG, "instance %d: history ids must stay below 2^32", i);
     work[i] = total;
     work[(size_t)s.n_inst + 1 + i] = first;
@@ -1447,25 +1523,26 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
       fill_common(&s, k);
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
+      k.test_flags = g_noalloc_test_flags.load();
       ce = launch_transport_f64(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
     } else {
       KParams<float> k{};
       fill_common(&s, k);
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
+      k.test_flags = g_noalloc_test_flags.load();
       ce = launch_transport_f32(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
     }
     if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
   }
   // the host copies above read pageable memory that dies with this call
   TP_CUDA(cudaStreamSynchronize(strm));
+  int status = 0;
+  TP_CUDA(cudaMemcpy(&status, s.d_status, sizeof status, cudaMemcpyDeviceToHost));
   if (counters_out) {
     unsigned long long h[kNumCounters];
-    int status = 0;
     TP_CUDA(cudaMemcpy(h, s.d_counters, sizeof h, cudaMemcpyDeviceToHost));
-    TP_CUDA(cudaMemcpy(&status, s.d_status, sizeof status, cudaMemcpyDeviceToHost));
     for (int i = 0; i < kNumCounters; ++i) counters_out[i] = (int64_t)h[i];
-    if (status != 0) return fail((tp_status)status, "a device-side wait gave up (status %d)", status);
   }
-  return TP_OK;
+  return device_status(status);
 }

@@ -131,6 +131,12 @@ struct KParams {
   tp_record* records;
   unsigned long long n_records;
   int* status;
+  // Host-written abort request (mapped pinned memory, may be null): once it is
+  // non-zero the kernels claim no new histories, finish the ones they hold and
+  // set *status to TP_ERR_ABORTED.
+  const volatile int* abort_flag;
+  // TP_TEST_* flags of tp_set_test_flags (0 in normal runs).
+  int test_flags;
 };
 
 // Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ,

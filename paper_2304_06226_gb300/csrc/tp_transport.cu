@@ -1085,15 +1085,44 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Returns false if the wait gave up (status set by the caller).
-__device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, uint64_t* bar) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Longest wait for the table copy: it takes microseconds, so a wait this long
+// means the copy never arrives.
+constexpr unsigned long long kStageWaitNs = 500ull * 1000ull * 1000ull;
+
+// Waits for phase 0 of the mbarrier, bounded in time and in tries; false if
+// it gave up.
+__device__ __forceinline__ bool wait_phase0(uint64_t* bar) {
+  uint32_t done = 0;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar))
+        : "memory");
+    if (!done && global_ns() - t0 > kStageWaitNs) break;
+  }
+  return done != 0;
+}
+
+// Copies `bytes` of scene tables into shared memory with one bulk asynchronous
+// copy completing on an mbarrier.  Returns false if the bounded wait gave up
+// (the caller records TP_ERR_TIMEOUT).  skip_copy (test hook) arms the barrier
+// without issuing the copy, so that the wait runs out with nothing in flight.
+__device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, uint64_t* bar, bool skip_copy) {
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !skip_copy) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
@@ -1103,16 +1132,20 @@ __device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, u
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
   }
-  // bounded wait on phase 0
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 20) && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar))
-        : "memory");
-  }
-  return __syncthreads_and(done) != 0;
+  bool ok = wait_phase0(bar);
+  // a copy that is late is still in flight: let it land (again bounded) before
+  // the block gives up and exits
+  if (!ok && !skip_copy) wait_phase0(bar);
+  return __syncthreads_and(ok) != 0;
+}
+
+// Host-requested stop (tp_abort): checked whenever new histories are claimed.
+// Records TP_ERR_ABORTED (unless an earlier error is recorded) and returns true.
+template <typename R>
+__device__ __forceinline__ bool aborted(const KParams<R>& kp) {
+  if (!kp.abort_flag || *kp.abort_flag == 0) return false;
+  atomicCAS(kp.status, 0, (int)TP_ERR_ABORTED);
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -1158,8 +1191,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
   __shared__ uint64_t bar;
   const uint8_t* base = kp.blob;
   if (kp.stage_blob) {
-    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
-      if (threadIdx.x == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar, (kp.test_flags & TP_TEST_SKIP_TABLE_COPY) != 0)) {
+      if (threadIdx.x == 0) atomicCAS(kp.status, 0, (int)TP_ERR_TIMEOUT);
       return;
     }
     base = smem;
@@ -1193,7 +1226,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
     while (idle) {
       if (chunk_next >= chunk_end) {
         unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+        if (lane == 0) b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
         b = __shfl_sync(kFull, b, 0);
         if (b >= total) {
           if (!alive) done = true;
@@ -1405,8 +1438,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
   const uint8_t* base = kp.blob;
   uint32_t tab = 0;
   if (kp.stage_blob) {
-    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
-      if (tid == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar, (kp.test_flags & TP_TEST_SKIP_TABLE_COPY) != 0)) {
+      if (tid == 0) atomicCAS(kp.status, 0, (int)TP_ERR_TIMEOUT);
       return;
     }
     base = smem;
@@ -1461,7 +1494,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       if (tid == 0) {
         claim_base = total;
         if (n_empty > 0 && claim_state == 0) {
-          const unsigned long long b = atomicAdd(kp.work_counter, (unsigned long long)n_empty);
+          const unsigned long long b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)n_empty);
           claim_base = b;
           if (b + n_empty >= total) claim_state = 1;
         }
@@ -1534,7 +1567,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       if (m) {
         const int leader = __ffs(m) - 1;
         unsigned long long g = 0;
-        if (lane == leader) g = atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
+        if (lane == leader) g = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
         g = __shfl_sync(kFull, g, leader) + __popc(m & ((1u << lane) - 1u));
         if (want) {
           if (g < total) slot_start(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
@@ -1576,8 +1609,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
   const uint8_t* base = kp.blob;
   uint32_t tab = 0;
   if (kp.stage_blob) {
-    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar)) {
-      if (threadIdx.x == 0) atomicExch(kp.status, (int)TP_ERR_TIMEOUT);
+    if (!stage_tables(smem, kp.blob, kp.blob_bytes, &bar, (kp.test_flags & TP_TEST_SKIP_TABLE_COPY) != 0)) {
+      if (threadIdx.x == 0) atomicCAS(kp.status, 0, (int)TP_ERR_TIMEOUT);
       return;
     }
     base = smem;
@@ -1667,7 +1700,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
       while (taken < n) {
         if (chunk_next >= chunk_end) {
           unsigned long long b = 0;
-          if (lane == 0) b = atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+          if (lane == 0) b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
           b = __shfl_sync(kFull, b, 0);
           if (b >= total) { work_left = false; break; }
           chunk_next = b;

@@ -199,8 +199,45 @@ class Scene:
         out["J2"] = out["J2"][: self.n_par]
         return out
 
+    def allreduce(self, histories_per_instance, group=None) -> None:
+        """Sum the accumulators of this scene over the ranks of `group` (each
+        rank ran disjoint history ids; histories_per_instance: what this rank
+        ran per instance) and load the sums back, so that tallies and the
+        backward pass give the statistics of all ranks' histories.  One FP64
+        all-reduce (shard.reduce_sums)."""
+        from . import shard
+        tb, ni, npar = self.total_bins, self.n_inst, self.n_par
+        parts = {"sum": torch.empty(ni, tb, dtype=torch.float64, device="cuda"),
+                 "sumsq": torch.empty(ni, tb, dtype=torch.float64, device="cuda"),
+                 "n": torch.as_tensor(np.broadcast_to(np.asarray(histories_per_instance, dtype=np.float64),
+                                                      (ni,)).copy(), device="cuda")}
+        if npar:
+            parts["J"] = torch.empty(ni, npar, tb, dtype=torch.float64, device="cuda")
+            parts["J2"] = torch.empty(ni, npar, tb, dtype=torch.float64, device="cuda")
+        for q in range(ni):
+            N.tp_read_raw(self.handle, q, parts["sum"][q].data_ptr(), parts["sumsq"][q].data_ptr(),
+                          parts["J"][q].data_ptr() if npar else None, parts["J2"][q].data_ptr() if npar else None,
+                          True)
+        shard.reduce_sums(parts, group)
+        n = parts["n"].cpu().numpy()
+        for q in range(ni):
+            N.tp_write_raw(self.handle, q, parts["sum"][q].data_ptr(), parts["sumsq"][q].data_ptr(),
+                           parts["J"][q].data_ptr() if npar else None, parts["J2"][q].data_ptr() if npar else None,
+                           float(n[q]), True)
+
     def counters(self) -> dict:
         return N.tp_get_counters(self.handle)
+
+    def status(self) -> tuple[dict, int]:
+        """(counters, device status) since the last reset; synchronises."""
+        return N.tp_get_counters_status(self.handle)
+
+    def abort(self) -> None:
+        """Stop the runs of this scene that are queued or running (tp_abort)."""
+        N.tp_abort(self.handle)
+
+    def set_test_flags(self, flags: int) -> None:
+        N.tp_set_test_flags(self.handle, flags)
 
     def launch(self) -> tuple[int, int, int]:
         """(kernel, block size, CTAs per SM) of the last run."""

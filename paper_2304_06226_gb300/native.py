@@ -10,9 +10,11 @@ from pathlib import Path
 
 LIB_PATH = Path(__file__).resolve().parent / "libtp.so"
 
-TP_OK, TP_ERR_INVALID_ARG, TP_ERR_GEOMETRY, TP_ERR_CUDA, TP_ERR_OOM, TP_ERR_TIMEOUT, TP_ERR_STATE = range(7)
+(TP_OK, TP_ERR_INVALID_ARG, TP_ERR_GEOMETRY, TP_ERR_CUDA, TP_ERR_OOM, TP_ERR_TIMEOUT, TP_ERR_STATE,
+ TP_ERR_ABORTED) = range(8)
 STATUS_NAMES = ["TP_OK", "TP_ERR_INVALID_ARG", "TP_ERR_GEOMETRY", "TP_ERR_CUDA", "TP_ERR_OOM",
-                "TP_ERR_TIMEOUT", "TP_ERR_STATE"]
+                "TP_ERR_TIMEOUT", "TP_ERR_STATE", "TP_ERR_ABORTED"]
+TP_TEST_SKIP_TABLE_COPY = 1
 TP_BOX, TP_TUBE, TP_SPHERE = 0, 1, 2
 TP_ROLE_BULK, TP_ROLE_DETECTOR, TP_ROLE_BLACK = 0, 1, 2
 TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3
@@ -95,6 +97,12 @@ class tp_run(C.Structure):
                 ("use_graph", C.c_int), ("secondaries", C.c_int)]
 
 
+class tp_peaks(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("fp32_fma", "int32_imad", "int32_logic", "mufu_lg2", "mufu_ex2",
+                                         "mufu_sin", "fp64_fma", "atomic_f64_spread", "atomic_f64_hot",
+                                         "l2_read_bytes", "sm_clock_mhz")] + [("sm_count", C.c_int)]
+
+
 SCENE_P = C.c_void_p
 DP = C.POINTER(C.c_double)
 
@@ -108,12 +116,17 @@ SIGNATURES = {
     "tp_read_raw": (C.c_int, [SCENE_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_int]),
     "tp_backward": (C.c_int, [SCENE_P, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "tp_write_raw": (C.c_int, [SCENE_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                               C.c_int]),
     "tp_set_params": (C.c_int, [SCENE_P, DP]),
     "tp_reset_tallies": (C.c_int, [SCENE_P]),
     "tp_get_counters": (C.c_int, [SCENE_P, C.POINTER(C.c_int64)]),
     "tp_get_launch": (C.c_int, [SCENE_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tp_total_bins": (C.c_int, [SCENE_P]),
     "tp_get_launch_count": (C.c_int, [SCENE_P]),
+    "tp_abort": (C.c_int, [SCENE_P]),
+    "tp_measure_peaks": (C.c_int, [C.POINTER(tp_peaks), C.c_void_p]),
+    "tp_set_test_flags": (C.c_int, [SCENE_P, C.c_int]),
     "tp_destroy_scene": (None, [SCENE_P]),
     "tp_last_error": (C.c_char_p, []),
     "tp_run_histories_noalloc": (C.c_int, [C.POINTER(tp_scene_desc), C.POINTER(tp_material), C.c_int,
@@ -183,6 +196,12 @@ def tp_read_raw(scene: int, instance: int, sum_ptr, sumsq_ptr, J_ptr, J2_ptr, on
           "tp_read_raw")
 
 
+def tp_write_raw(scene: int, instance: int, sum_ptr, sumsq_ptr, J_ptr, J2_ptr, n_histories: float,
+                 on_device: bool) -> None:
+    check(lib.tp_write_raw(scene, instance, sum_ptr, sumsq_ptr, J_ptr, J2_ptr, float(n_histories), int(on_device)),
+          "tp_write_raw")
+
+
 def tp_backward(scene: int, grad_ptr: int, out_ptr: int, on_device: bool, stream: int | None) -> None:
     check(lib.tp_backward(scene, grad_ptr, out_ptr, int(on_device), stream), "tp_backward")
 
@@ -201,6 +220,28 @@ def tp_get_counters(scene: int) -> dict:
     out = (C.c_int64 * 8)()
     check(lib.tp_get_counters(scene, out), "tp_get_counters")
     return dict(zip(COUNTER_NAMES, list(out)))
+
+
+def tp_abort(scene: int) -> None:
+    check(lib.tp_abort(scene), "tp_abort")
+
+
+def tp_set_test_flags(scene: int | None, flags: int) -> None:
+    check(lib.tp_set_test_flags(scene, flags), "tp_set_test_flags")
+
+
+def tp_get_counters_status(scene: int) -> tuple[dict, int]:
+    """Counters and the device status of the runs since the last reset
+    (tp_get_counters without raising)."""
+    out = (C.c_int64 * 8)()
+    st = lib.tp_get_counters(scene, out)
+    return dict(zip(COUNTER_NAMES, list(out))), st
+
+
+def tp_measure_peaks(stream: int | None = None) -> dict:
+    out = tp_peaks()
+    check(lib.tp_measure_peaks(C.byref(out), stream), "tp_measure_peaks")
+    return {n: getattr(out, n) for n, _ in tp_peaks._fields_}
 
 
 def tp_get_launch(scene: int) -> tuple[int, int, int]:
