@@ -712,7 +712,10 @@ static void transport(ctx* c, particle* P, uint64_t hid, or_record* rec, uint32_
         }
       }
       if (j == OR_P_ABS) { end = OR_END_ABSORBED; break; }
-      if (j == OR_P_INC) {
+      if (j == OR_P_INC && s->mats[mat].rod) {
+        /* rod model (test mode): forward or backward along z, 1/2 each */
+        P->u[0] = 0.0; P->u[1] = 0.0; P->u[2] = (xi[2] < 0.5) ? -1.0 : 1.0;
+      } else if (j == OR_P_INC) {
         /* isotropic: cos theta uniform on [-1,1], azimuth uniform */
         double mu = 2.0 * xi[2] - 1.0, phi = 2.0 * PI * xi[3];
         double st = sqrt(fmax(0.0, 1.0 - mu * mu));

@@ -76,6 +76,9 @@ typedef struct {
   double V0;            /* unit cell volume, A^3 */
   const double *d, *mult, *F2;   /* per line: d (A), multiplicity, |F|^2 (barn) */
   int density_par, scale_par;    /* parameter index or -1 */
+  int rod;              /* test mode, 0 normally: incoherent scattering sends the neutron
+                           along +z or -z with probability 1/2 each (the rod model whose
+                           two-stream closed form pins the scatter-and-continue loop) */
 } or_material;
 
 typedef struct {

@@ -7,6 +7,7 @@ own structures; nothing here comes from the CUDA package.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -60,7 +61,7 @@ class Material(C.Structure):
     _fields_ = [("sig_abs_ref", C.c_double), ("abs_1v", C.c_int), ("sig_inc", C.c_double),
                 ("nlines", C.c_int), ("V0", C.c_double), ("d", C.POINTER(C.c_double)),
                 ("mult", C.POINTER(C.c_double)), ("F2", C.POINTER(C.c_double)),
-                ("density_par", C.c_int), ("scale_par", C.c_int)]
+                ("density_par", C.c_int), ("scale_par", C.c_int), ("rod", C.c_int)]
 
 
 class Chopper(C.Structure):
@@ -109,31 +110,48 @@ class Accum(C.Structure):
 _lib = None
 
 
+def _load(path) -> C.CDLL:
+    L = C.CDLL(str(path))
+    dp = C.POINTER(C.c_double)
+    L.or_run.argtypes = [C.POINTER(Scene), C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int,
+                         C.c_int, C.POINTER(Accum), C.POINTER(Record)]
+    L.or_run.restype = C.c_int
+    L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                   C.POINTER(C.c_uint32)]
+    L.or_u01.argtypes = [C.c_uint32]
+    L.or_u01.restype = C.c_double
+    L.or_sigma.argtypes = [C.POINTER(Scene), C.c_int, dp, C.c_double, dp]
+    L.or_mirror_R.argtypes = [C.POINTER(Mirror), C.c_double]
+    L.or_mirror_R.restype = C.c_double
+    for fn in ("or_prim_exit", "or_prim_entry"):
+        f = getattr(L, fn)
+        f.argtypes = [C.POINTER(Scene), C.POINTER(Prim), dp, dp, dp, C.POINTER(C.c_int)]
+        f.restype = C.c_double
+    L.or_prim_inside.argtypes = [C.POINTER(Scene), C.POINTER(Prim), dp, dp]
+    L.or_prim_inside.restype = C.c_int
+    L.or_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
+    L.or_total_bins.argtypes = [C.POINTER(Scene)]
+    L.or_total_bins.restype = C.c_int
+    return L
+
+
+@contextlib.contextmanager
+def use_library(path):
+    """Run the oracle calls inside the block with another build of oracle.c
+    (the tests' planted-mistake copies), then restore the regular one."""
+    global _lib
+    old = _lib
+    _lib = _load(path)
+    try:
+        yield _lib
+    finally:
+        _lib = old
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(str(build()))
-        dp = C.POINTER(C.c_double)
-        L.or_run.argtypes = [C.POINTER(Scene), C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int,
-                             C.c_int, C.POINTER(Accum), C.POINTER(Record)]
-        L.or_run.restype = C.c_int
-        L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
-                                       C.POINTER(C.c_uint32)]
-        L.or_u01.argtypes = [C.c_uint32]
-        L.or_u01.restype = C.c_double
-        L.or_sigma.argtypes = [C.POINTER(Scene), C.c_int, dp, C.c_double, dp]
-        L.or_mirror_R.argtypes = [C.POINTER(Mirror), C.c_double]
-        L.or_mirror_R.restype = C.c_double
-        for fn in ("or_prim_exit", "or_prim_entry"):
-            f = getattr(L, fn)
-            f.argtypes = [C.POINTER(Scene), C.POINTER(Prim), dp, dp, dp, C.POINTER(C.c_int)]
-            f.restype = C.c_double
-        L.or_prim_inside.argtypes = [C.POINTER(Scene), C.POINTER(Prim), dp, dp]
-        L.or_prim_inside.restype = C.c_int
-        L.or_rotate.argtypes = [dp, C.c_double, C.c_double, dp]
-        L.or_total_bins.argtypes = [C.POINTER(Scene)]
-        L.or_total_bins.restype = C.c_int
-        _lib = L
+        _lib = _load(build())
     return _lib
 
 
@@ -198,10 +216,11 @@ class OracleScene:
                 self._keep += [d, mu, f2]
                 MA[i] = Material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"), m["sigma_inc"],
                                  len(d), br["V0"], _dptr(d), _dptr(mu), _dptr(f2),
-                                 m["density_param"], m["scale_param"])
+                                 m["density_param"], m["scale_param"], int(m.get("rod", False)))
             else:
                 MA[i] = Material(m["sigma_abs_ref"], int(m["abs_mode"] == "1/v"), m["sigma_inc"],
-                                 0, 1.0, None, None, None, m["density_param"], m["scale_param"])
+                                 0, 1.0, None, None, None, m["density_param"], m["scale_param"],
+                                 int(m.get("rod", False)))
         bias = np.ascontiguousarray(desc["bias"], dtype=np.float64).reshape(-1)
         if bias.size == 0:
             bias = np.ones(3)
