@@ -195,21 +195,22 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     sc = Scene(desc)
     bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
     runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
-                                   graph=True, first=first, secondaries=args.secondaries)) if grad else None
+                                   graph=True, first=first, seed=seed, secondaries=args.secondaries)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-    first = 0
+    first, seed = 0, None
+    n_max = int(np.max(desc["instances"]["counts"]))   # ids per instance and rank
 
     def step(k, st=None):
-        # every step and every rank takes its own history ids (weak scaling):
-        # the tallies then hold steps x ranks x n distinct histories
-        nonlocal first
-        first = shard.step_first(k, rank, world, n)
+        # every step and every rank runs its own histories (weak scaling): the
+        # tallies then hold steps x ranks x n distinct histories
+        nonlocal first, seed
+        seed, first = shard.step_stream(k, rank, world, n_max, sc.seed)
         if grad:
             runs(st)
             sc.backward(bgrad, stream=st)
         else:
-            sc.run(n, first=first, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
+            sc.run(n, first=first, seed=seed, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
 
     peaks = measured_peaks() if rank == 0 else None
     # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
@@ -267,13 +268,13 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     host_grad = np.empty((sc.n_inst, max(1, sc.n_par)))
     for k in range(e2e_steps):
         sc.reset()
-        first = shard.step_first(args.steps + k, rank, world, n)
+        seed, first = shard.step_stream(args.warmup + args.steps + k, rank, world, n_max, sc.seed)
         if grad:
             runs()
             g = sc.backward(bgrad)
             host_grad[:, : sc.n_par] = g.cpu().numpy()
         else:
-            sc.run(n, first=first, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
+            sc.run(n, first=first, seed=seed, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
         for t in range(len(sc.tally_bins)):
             o = sc.tally_off[t]
             NN.tp_read_tallies(sc.handle, t, q, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
@@ -355,11 +356,10 @@ def run_batched(args, W, Scene, torch, peaks) -> dict:
     steps = max(1, args.batched_steps)
     a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     fw_ms, bw_ms = [], []
-    span = int(counts.max())
     for k in range(steps):
         a.record(stream)
-        # one CUDA graph per step, replayed with new first ids: each step runs distinct histories
-        sc.run(want_grad=True, stream=stream, graph=True, first=k * span)
+        # the step's CUDA graph, its own Philox key per step: each step runs distinct histories
+        sc.run(want_grad=True, stream=stream, graph=True, seed=sc.seed + 1000 + k)
         b.record(stream)
         sc.backward(grad, stream=stream)
         c.record(stream)

@@ -353,8 +353,10 @@ tp_status tp_abort(tp_scene* s);
  * scene tables into shared memory but issue no copy, so that the bounded wait
  * (about half a second) runs out: each block records TP_ERR_TIMEOUT and
  * returns with nothing in flight and nothing transported.  s = NULL sets the
- * flags of tp_run_histories_noalloc, which has no scene. */
-enum { TP_TEST_SKIP_TABLE_COPY = 1 };
+ * flags of tp_run_histories_noalloc, which has no scene.
+ * TP_TEST_FULL_BUILD: the scene runs the kernels' complete feature build even
+ * if the lean one serves it (the two must agree; the test of that uses it). */
+enum { TP_TEST_SKIP_TABLE_COPY = 1, TP_TEST_FULL_BUILD = 2 };
 tp_status tp_set_test_flags(tp_scene* s, int flags);
 
 /* Launch configuration of the last run: kernel (TP_KERNEL_*), block size and

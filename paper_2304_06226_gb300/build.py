@@ -17,10 +17,19 @@ LIB = PKG / "libtp.so"
 OBJDIR = PKG / "_build"
 # (source, object, extra flags): the transport kernels are compiled once per
 # precision so that the halves build in parallel
-UNITS = [("tp_transport.cu", "tp_transport_f32.o", ["-DTP_BUILD_F32"]),
-         ("tp_transport.cu", "tp_transport_f64.o", ["-DTP_BUILD_F64"]),
-         ("tp_api.cu", "tp_api.o", []),
-         ("tp_peaks.cu", "tp_peaks.o", [])]
+# The transport kernels are compiled once per (precision, kernel family) so
+# that the units build in parallel; the FP32 transport takes the hardware's
+# division and square root (within 2 ulp) instead of the IEEE-rounded
+# sequences: shorter code in the hot loop, far below the FP32 path's own
+# geometric rounding.  FP64 keeps IEEE rounding (its histories match the FP64
+# oracle to 1e-9).
+_F32 = ["-DTP_BUILD_F32", "-prec-div=false", "-prec-sqrt=false"]
+UNITS = ([("tp_transport.cu", f"tp_transport_f32_k{k}.o", _F32 + [f"-DTP_BUILD_KERNEL={k}"]) for k in (1, 2, 3)]
+         + [("tp_transport.cu", f"tp_transport_f64_k{k}.o", ["-DTP_BUILD_F64", f"-DTP_BUILD_KERNEL={k}"])
+            for k in (1, 2, 3)]
+         + [("tp_transport.cu", "tp_transport_common.o", ["-DTP_BUILD_COMMON"]),
+            ("tp_api.cu", "tp_api.o", []),
+            ("tp_peaks.cu", "tp_peaks.o", [])])
 SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,7 +45,8 @@ def _stale() -> bool:
     if not LIB.exists():
         return True
     t = LIB.stat().st_mtime
-    deps = [CSRC / f for f in SOURCES] + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list(INCLUDE.glob("*.h"))
+    deps = ([CSRC / f for f in SOURCES] + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list(INCLUDE.glob("*.h"))
+            + [Path(__file__)])
     return any(d.stat().st_mtime > t for d in deps)
 
 

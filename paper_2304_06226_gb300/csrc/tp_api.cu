@@ -101,7 +101,8 @@ struct LaunchCfg {
   int stage;   // copy the scene tables into shared memory
   int hi;      // the 64-register build (FP32 runs only)
   int defer;   // gradient runs: secondaries queued and transported in a second pass
-  int variant() const { return kernel | (hi ? kVariantHighOcc : 0); }
+  int full = 1;  // the build with every feature (else the lean one)
+  int variant() const { return kernel | (hi ? kVariantHighOcc : 0) | (full ? kVariantFull : 0); }
 };
 
 struct tp_scene {
@@ -109,6 +110,11 @@ struct tp_scene {
   int sm_count = 0;
   int precision = TP_FP32;
   int event_cap = 4096;
+  // 1 if the scene needs the kernels' full feature set (mirrors, choppers,
+  // scorers other than count / angular / PSD, moderator / Maxwellian /
+  // divergent guns or an aperture), 0 if the lean build serves it
+  int full = 1;
+  int full_needed = 1;   // what the description needs (full may be forced by a test flag)
   // description (owned copies)
   int world_shape = TP_BOX;
   double world_c[3] = {0, 0, 0}, world_p[3] = {0, 0, 0};
@@ -639,7 +645,8 @@ tp_status pick_launch(tp_scene* s, bool grad, int req_block, int req_ctas, int* 
   int b = req_block > 0 ? req_block : (s->block > 0 ? s->block : 256);
   if (b % 32 != 0 || b < 32 || b > 256) return fail(TP_ERR_INVALID_ARG, "block_size %d: need a multiple of 32 in [32, 256]", b);
   int occ = 0;
-  TP_CUDA(occupancy_transport(TP_KERNEL_HISTORY, s->precision, grad, s->grid_cells > 0, b, smem_bytes(s), &occ));
+  TP_CUDA(occupancy_transport(TP_KERNEL_HISTORY | (s->full ? kVariantFull : 0), s->precision, grad,
+                              s->grid_cells > 0, b, smem_bytes(s), &occ));
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "block_size %d does not fit on an SM", b);
   int c = req_ctas > 0 ? std::min(req_ctas, occ) : occ;
   *block = b;
@@ -680,14 +687,15 @@ tp_status resolve(tp_scene* s, bool grad, int kernel, int req_block, int req_cta
   if (hi > 0 && !can_hi) return fail(TP_ERR_INVALID_ARG, "the 64-register build serves FP32 runs only");
   int h = hi > 0 ? 1 : 0, occ = 0;
   const size_t sm = smem_variant(s, kernel, grad, b, stage);
-  TP_CUDA(occupancy_transport(kernel | (h ? kVariantHighOcc : 0), s->precision, grad, s->grid_cells > 0, b, sm, &occ));
+  const int fbit = s->full ? kVariantFull : 0;
+  TP_CUDA(occupancy_transport(kernel | (h ? kVariantHighOcc : 0) | fbit, s->precision, grad, s->grid_cells > 0, b, sm, &occ));
   if (hi < 0 && can_hi && req_ctas > occ) {
     int occ_hi = 0;
-    TP_CUDA(occupancy_transport(kernel | kVariantHighOcc, s->precision, grad, s->grid_cells > 0, b, sm, &occ_hi));
+    TP_CUDA(occupancy_transport(kernel | kVariantHighOcc | fbit, s->precision, grad, s->grid_cells > 0, b, sm, &occ_hi));
     if (occ_hi > occ) { h = 1; occ = occ_hi; }
   }
   if (occ < 1) return fail(TP_ERR_INVALID_ARG, "kernel %d block_size %d does not fit on an SM", kernel, b);
-  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage, h, 0};
+  *c = LaunchCfg{kernel, b, req_ctas > 0 ? std::min(req_ctas, occ) : occ, stage, h, 0, s->full};
   return TP_OK;
 }
 
@@ -1008,6 +1016,16 @@ static tp_status describe(const tp_scene_desc* d, tp_scene* s) {
   }
   if (tb > (1ll << 30)) return (fail(TP_ERR_INVALID_ARG, "too many bins"));
   s->total_bins = (int)tb;
+  {
+    bool full = d->n_mirrors > 0 || d->n_choppers > 0;
+    for (const tp_prim& p : s->prims) full = full || p.mirror >= 0 || p.chopper >= 0;
+    for (const tp_tally_desc& T : s->tallies)
+      full = full || !(T.kind == TP_TALLY_COUNT || T.kind == TP_TALLY_ANGULAR || T.kind == TP_TALLY_PSD);
+    const tp_source& g = s->source;
+    full = full || g.kind == TP_SRC_MODERATOR || g.temperature > 0 || g.div[0] > 0 || g.div[1] > 0 || g.has_aperture;
+    s->full_needed = full ? 1 : 0;
+    s->full = s->full_needed;
+  }
   s->tally_off[s->tallies.size()] = (int)tb;
   return validate_geometry(s);
 }
@@ -1365,12 +1383,15 @@ tp_status tp_abort(tp_scene* s) {
 
 tp_status tp_set_test_flags(tp_scene* s, int flags) {
   g_err.clear();
-  if (flags & ~TP_TEST_SKIP_TABLE_COPY) return fail(TP_ERR_INVALID_ARG, "unknown test flags %#x", flags);
+  if (flags & ~(TP_TEST_SKIP_TABLE_COPY | TP_TEST_FULL_BUILD))
+    return fail(TP_ERR_INVALID_ARG, "unknown test flags %#x", flags);
   if (!s) {
-    g_noalloc_test_flags.store(flags);
+    g_noalloc_test_flags.store(flags & TP_TEST_SKIP_TABLE_COPY);
     return TP_OK;
   }
   s->test_flags = flags;
+  s->full = (s->full_needed || (flags & TP_TEST_FULL_BUILD)) ? 1 : 0;
+  for (int g = 0; g < 2; ++g) s->tuned_kernel[g] = 0;   // the autotuner's choice was for the other build
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }   // the flags are baked into it
   return TP_OK;
 }
@@ -1524,14 +1545,14 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
       k.test_flags = g_noalloc_test_flags.load();
-      ce = launch_transport_f64(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
+      ce = launch_transport_f64(k, TP_KERNEL_HISTORY | (s.full ? kVariantFull : 0), false, grid, block, smem_bytes(&s), strm);
     } else {
       KParams<float> k{};
       fill_common(&s, k);
       k.key0 = (uint32_t)(r->seed & 0xffffffffu); k.key1 = (uint32_t)(r->seed >> 32);
       k.total = total; k.chunk = (int)chunk;
       k.test_flags = g_noalloc_test_flags.load();
-      ce = launch_transport_f32(k, TP_KERNEL_HISTORY, false, grid, block, smem_bytes(&s), strm);
+      ce = launch_transport_f32(k, TP_KERNEL_HISTORY | (s.full ? kVariantFull : 0), false, grid, block, smem_bytes(&s), strm);
     }
     if (ce != cudaSuccess) return fail(TP_ERR_CUDA, "transport launch: %s", cudaGetErrorString(ce));
   }

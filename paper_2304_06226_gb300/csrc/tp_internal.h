@@ -140,13 +140,29 @@ struct KParams {
 };
 
 // Launchers (tp_transport.cu).  variant: TP_KERNEL_HISTORY / _EVENT / _WARPQ,
-// optionally with kVariantHighOcc: the 64-register build of an FP32 kernel
-// (4 blocks of 256 threads per SM instead of 3).
+// optionally with kVariantHighOcc (the 64-register build of an FP32 kernel: 4
+// blocks of 256 threads per SM instead of 3) and kVariantFull (the build with
+// every feature: mirrors, choppers, all scorer kinds and guns; without it the
+// lean build, for scenes that use none of them).
 constexpr int kVariantHighOcc = 16;
+constexpr int kVariantFull = 32;
 cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
 cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block,
                                  size_t smem, cudaStream_t st);
+// one per kernel family (k1 history, k2 event, k3 warp pools), each in its own
+// translation unit
+#define TP_DECLARE_FAMILY(K)                                                                                \
+  cudaError_t launch_transport_f32_##K(const KParams<float>& p, int variant, bool grad, int grid, int block, \
+                                       size_t smem, cudaStream_t st);                                       \
+  cudaError_t launch_transport_f64_##K(const KParams<double>& p, int variant, bool grad, int grid, int block, \
+                                       size_t smem, cudaStream_t st);                                       \
+  cudaError_t occupancy_f32_##K(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas);  \
+  cudaError_t occupancy_f64_##K(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas);
+TP_DECLARE_FAMILY(k1)
+TP_DECLARE_FAMILY(k2)
+TP_DECLARE_FAMILY(k3)
+#undef TP_DECLARE_FAMILY
 // Shared memory of the neutron bank of a variant (added to the staged tables).
 size_t bank_bytes(int variant, int precision, bool grad, int block);
 // Bytes of one queued neutron record (sec_buf).

@@ -38,6 +38,16 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Compile-time options of a kernel build (template parameter OPT): kOptGrid
+// walks the uniform grid of a large scene; kOptFull compiles the complete
+// feature set -- supermirrors, disk choppers, every scorer kind and the
+// moderator / Maxwellian / divergent guns with their apertures.  Without it
+// (the lean build, chosen by the host for scenes that use none of those) the
+// kernel carries only boxes, tubes and spheres, count / angular / PSD scorers
+// and pencil or rectangle guns, a smaller instruction footprint for the hot
+// loop.  Both builds compute the same thing for the scenes they accept.
+constexpr int kOptGrid = 1, kOptFull = 2;
+
 // ---------------------------------------------------------------------------
 // Precision traits
 // ---------------------------------------------------------------------------
@@ -526,28 +536,37 @@ __device__ __forceinline__ R tally_angle(const DTally<R>& T, R x0, R x1, R x2) {
   return d_atan2(d_sqrt(c0 * c0 + c1 * c1 + c2 * c2), dt);
 }
 
-template <typename R>
+template <typename R, int OPT>
 __device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R lam, int nscat, R path) {
-  switch (T.kind) {
-    case TP_TALLY_COUNT: return 0;
-    case TP_TALLY_TOF: return bin1(path * lam * R(1.0 / kHoverMn), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-    case TP_TALLY_ANGULAR: return bin1(tally_angle(T, x0, x1, x2), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-    case TP_TALLY_MULTISCAT: return bin1((R)nscat, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-    case TP_TALLY_DQ: {
-      // elastic momentum transfer Q = 4 pi sin(theta/2) / lambda (Eq. eQelastic)
-      R sh, ch;
-      d_sincos(R(0.5) * tally_angle(T, x0, x1, x2), &sh, &ch);
-      return bin1(Tr<R>::kFourPi * sh / lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-    }
-    case TP_TALLY_PSD: {
-      const int bx = bin1(x0, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-      const int by = bin1(x1, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
-      return (bx < 0 || by < 0) ? -1 : bx * T.nb1 + by;
-    }
-    default: {
-      const int bl = bin1(lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
-      const int bx = bin1(x0, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
-      return (bl < 0 || bx < 0) ? -1 : bl * T.nb1 + bx;
+  if constexpr (!(OPT & kOptFull)) {
+    // lean build: count, angular and PSD scorers only
+    if (T.kind == TP_TALLY_COUNT) return 0;
+    if (T.kind == TP_TALLY_ANGULAR) return bin1(tally_angle(T, x0, x1, x2), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    const int bx = bin1(x0, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+    const int by = bin1(x1, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+    return (bx < 0 || by < 0) ? -1 : bx * T.nb1 + by;
+  } else {
+    switch (T.kind) {
+      case TP_TALLY_COUNT: return 0;
+      case TP_TALLY_TOF: return bin1(path * lam * R(1.0 / kHoverMn), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      case TP_TALLY_ANGULAR: return bin1(tally_angle(T, x0, x1, x2), T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      case TP_TALLY_MULTISCAT: return bin1((R)nscat, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      case TP_TALLY_DQ: {
+        // elastic momentum transfer Q = 4 pi sin(theta/2) / lambda (Eq. eQelastic)
+        R sh, ch;
+        d_sincos(R(0.5) * tally_angle(T, x0, x1, x2), &sh, &ch);
+        return bin1(Tr<R>::kFourPi * sh / lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+      }
+      case TP_TALLY_PSD: {
+        const int bx = bin1(x0, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+        const int by = bin1(x1, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+        return (bx < 0 || by < 0) ? -1 : bx * T.nb1 + by;
+      }
+      default: {
+        const int bl = bin1(lam, T.lo[0], T.hi[0], T.inv_w[0], T.nb0);
+        const int bx = bin1(x0, T.lo[1], T.hi[1], T.inv_w[1], T.nb1);
+        return (bl < 0 || bx < 0) ? -1 : bl * T.nb1 + bx;
+      }
     }
   }
 }
@@ -555,7 +574,7 @@ __device__ __forceinline__ int tally_bin(const DTally<R>& T, R x0, R x1, R x2, R
 // Scoring at a particle tracing state: every tally of `mask` (filtered by face
 // and scattering number) gets w and w^2 in its bin, and the gradient tallies
 // w A_p (a derivative secondary scores w into the radius tally only).
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, int OPT>
 __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>* tallies, unsigned mask, int face,
                                        R x0, R x1, R x2, R lam, R w_, R A0, R A1, R A2, R A3, int nscat,
                                        uint32_t inst, bool secondary, R path) {
@@ -566,7 +585,7 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     const DTally<R>& T = tallies[t];
     if (T.face >= 0 && T.face != face) continue;
     if (T.scat >= 0 && T.scat != nscat) continue;
-    const int b = tally_bin(T, x0, x1, x2, lam, nscat, path);
+    const int b = tally_bin<R, OPT>(T, x0, x1, x2, lam, nscat, path);
     if (b < 0) continue;
     const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
     const R w = w_;
@@ -587,17 +606,17 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
   }
 }
 
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, int OPT>
 __device__ __forceinline__ void score(const KParams<R>& kp, const View<R>& V, const Particle<R>& P, unsigned mask,
                                       int face) {
-  score_out<R, GRAD>(kp, V.tallies, mask, face, P.x[0], P.x[1], P.x[2], P.lam, P.w, P.A[0], P.A[1], P.A[2],
+  score_out<R, GRAD, OPT>(kp, V.tallies, mask, face, P.x[0], P.x[1], P.x[2], P.lam, P.w, P.A[0], P.A[1], P.A[2],
                      P.A[3], P.nscat, P.inst, P.sub0 != 0u, P.s);
 }
 
 // ---------------------------------------------------------------------------
 // Source (event 0), §3.2
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, int OPT>
 __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R dR, int* end) {
   const uint4 a = philox(make_uint4(0u, 0u, P.hid, P.inst), kp.key0, kp.key1);
   P.x[0] = kp.src_c[0]; P.x[1] = kp.src_c[1]; P.x[2] = kp.src_c[2];
@@ -605,42 +624,49 @@ __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R
     P.x[0] += kp.src_half[0] * (R(2) * Tr<R>::u01(a.x) - R(1));
     P.x[1] += kp.src_half[1] * (R(2) * Tr<R>::u01(a.y) - R(1));
   }
-  const bool need_b = kp.src_kind == TP_SRC_MODERATOR || kp.src_kT > R(0) || kp.src_div[0] > R(0) ||
-                      kp.src_div[1] > R(0);
-  uint4 b = make_uint4(0u, 0u, 0u, 0u);
-  if (need_b) b = philox(make_uint4(0u, 1u, P.hid, P.inst), kp.key0, kp.key1);
-  if (kp.src_kT > R(0)) {
-    // Maxwell-Boltzmann energies sqrt(E) exp(-E/kT): E/kT ~ Gamma(3/2) = an
-    // exponential variate plus half a squared normal one (Box-Muller)
-    R sc, cc;
-    d_sincos(R(0.5) * Tr<R>::kPi * Tr<R>::u01(b.w), &sc, &cc);
-    const R e = kp.src_kT * (-d_log(Tr<R>::u01(a.z)) - d_log(Tr<R>::u01(a.w)) * cc * cc);
-    P.lam = d_sqrt(R(kH2over2mn) / e);
+  if constexpr (OPT & kOptFull) {
+    const bool need_b = kp.src_kind == TP_SRC_MODERATOR || kp.src_kT > R(0) || kp.src_div[0] > R(0) ||
+                        kp.src_div[1] > R(0);
+    uint4 b = make_uint4(0u, 0u, 0u, 0u);
+    if (need_b) b = philox(make_uint4(0u, 1u, P.hid, P.inst), kp.key0, kp.key1);
+    if (kp.src_kT > R(0)) {
+      // Maxwell-Boltzmann energies sqrt(E) exp(-E/kT): E/kT ~ Gamma(3/2) = an
+      // exponential variate plus half a squared normal one (Box-Muller)
+      R sc, cc;
+      d_sincos(R(0.5) * Tr<R>::kPi * Tr<R>::u01(b.w), &sc, &cc);
+      const R e = kp.src_kT * (-d_log(Tr<R>::u01(a.z)) - d_log(Tr<R>::u01(a.w)) * cc * cc);
+      P.lam = d_sqrt(R(kH2over2mn) / e);
+    } else {
+      P.lam = kp.src_lam_hi > kp.src_lam_lo ? kp.src_lam_lo + (kp.src_lam_hi - kp.src_lam_lo) * Tr<R>::u01(a.z)
+                                            : kp.src_lam_lo;
+    }
+    if (kp.src_kind == TP_SRC_MODERATOR) {
+      // towards a point uniform on the slit
+      const R d0 = kp.src_c[0] + kp.src_slit_half[0] * (R(2) * Tr<R>::u01(b.y) - R(1)) - P.x[0];
+      const R d1 = kp.src_c[1] + kp.src_slit_half[1] * (R(2) * Tr<R>::u01(b.z) - R(1)) - P.x[1];
+      const R d2 = kp.src_slit_z - P.x[2];
+      const R inv = R(1) / d_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      P.u[0] = d0 * inv; P.u[1] = d1 * inv; P.u[2] = d2 * inv;
+    } else if (kp.src_div[0] > R(0) || kp.src_div[1] > R(0)) {
+      const R tx = d_tan(kp.src_div[0] * (R(2) * Tr<R>::u01(a.w) - R(1)));
+      const R ty = d_tan(kp.src_div[1] * (R(2) * Tr<R>::u01(b.x) - R(1)));
+      const R inv = R(1) / d_sqrt(tx * tx + ty * ty + R(1));
+      P.u[0] = tx * inv; P.u[1] = ty * inv; P.u[2] = inv;
+    } else {
+      P.u[0] = R(0); P.u[1] = R(0); P.u[2] = R(1);
+    }
   } else {
+    // lean build: uniform wavelength band, direction +z
     P.lam = kp.src_lam_hi > kp.src_lam_lo ? kp.src_lam_lo + (kp.src_lam_hi - kp.src_lam_lo) * Tr<R>::u01(a.z)
                                           : kp.src_lam_lo;
-  }
-  if (kp.src_kind == TP_SRC_MODERATOR) {
-    // towards a point uniform on the slit
-    const R d0 = kp.src_c[0] + kp.src_slit_half[0] * (R(2) * Tr<R>::u01(b.y) - R(1)) - P.x[0];
-    const R d1 = kp.src_c[1] + kp.src_slit_half[1] * (R(2) * Tr<R>::u01(b.z) - R(1)) - P.x[1];
-    const R d2 = kp.src_slit_z - P.x[2];
-    const R inv = R(1) / d_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    P.u[0] = d0 * inv; P.u[1] = d1 * inv; P.u[2] = d2 * inv;
-  } else if (kp.src_div[0] > R(0) || kp.src_div[1] > R(0)) {
-    const R tx = d_tan(kp.src_div[0] * (R(2) * Tr<R>::u01(a.w) - R(1)));
-    const R ty = d_tan(kp.src_div[1] * (R(2) * Tr<R>::u01(b.x) - R(1)));
-    const R inv = R(1) / d_sqrt(tx * tx + ty * ty + R(1));
-    P.u[0] = tx * inv; P.u[1] = ty * inv; P.u[2] = inv;
-  } else {
     P.u[0] = R(0); P.u[1] = R(0); P.u[2] = R(1);
   }
   P.w = R(1);
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
   P.nscat = 0; P.k = 0; P.sub0 = 0; P.nsec = 0; P.s = R(0); P.last = kNoPrim;
-  if (kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
-                          fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
+  if ((OPT & kOptFull) && kp.src_aperture && (fabs(P.x[0] - kp.src_c[0]) > kp.src_ap[0] ||
+                                              fabs(P.x[1] - kp.src_c[1]) > kp.src_ap[1])) {
     P.w = R(0);
     *end = END_APERTURE;
     return false;
@@ -694,7 +720,7 @@ __device__ __forceinline__ void scatter_dir(const View<R>& V, int mat, int proc,
 template <typename R>
 __device__ __forceinline__ bool radius_crossing(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar],
                                 R dR, int mi, int mo, const R n[3], Particle<R>* S,
-                                unsigned long long* cnt) {
+                                unsigned* cnt) {
   const R cosn = fabs(P.u[0] * n[0] + P.u[1] * n[1] + P.u[2] * n[2]);
   if (cosn < R(1e-12)) return false;
   R si[TP_NPROC] = {R(0), R(0), R(0)}, so[TP_NPROC] = {R(0), R(0), R(0)};
@@ -859,14 +885,13 @@ struct Adv {
 // is (the regrouping kernels), which drops the other branch from the code.
 constexpr int kAny = 0, kInPrim = 1, kInWorld = 2;
 
-template <typename R, bool GRAD, bool GRID, int WHERE = kAny>
+template <typename R, bool GRAD, int OPT, int WHERE = kAny>
 __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
-                       unsigned long long* cnt, Adv<R>& a) {
+                       unsigned* cnt, Adv<R>& a) {
   const R INF = Tr<R>::inf();
   P.k += 1;
   if ((int)P.k > kp.event_cap) { cnt[C_TRUNC]++; return END_TRUNCATED; }
   cnt[C_EVENTS]++;
-  a.r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
   const int mat = (WHERE == kInWorld) ? -1 : (P.vol >= 0 ? V.prims[P.vol].material : -1);
   R* sig = a.sig;
   sig[0] = sig[1] = sig[2] = R(0);
@@ -878,7 +903,14 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
     sig_g = m.g[0] * sig[0] + m.g[1] * sig[1] + m.g[2] * sig[2];
   }
   a.sig_g = sig_g;
-  const R l = sig_g > R(0) ? -d_log(Tr<R>::u01(a.r0.x)) / sig_g : INF;
+  // Random numbers only where a flight is sampled: with Sigma_g = 0 (vacuum,
+  // or every bias factor 0) the step is infinite and the event draws nothing.
+  // The counter-based stream keeps every other event's numbers unchanged.
+  R l = INF;
+  if (sig_g > R(0)) {
+    a.r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
+    l = -d_log(Tr<R>::u01(a.r0.x)) / sig_g;
+  }
   // next boundary
   R db;
   int target = -3, face = -1;
@@ -889,7 +921,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
     const R tmin = R(2) * nudge_len(P.x);
     const int last = P.last & kPrimMask;
     const bool last_hull = (P.last & kLastHull) != 0;
-    if constexpr (GRID) {
+    if constexpr ((OPT & kOptGrid) != 0) {
       grid_search(kp, V, dR, P.x[0], P.x[1], P.x[2], P.u[0], P.u[1], P.u[2], last, last_hull, tmin, &db,
                   &target, &face);
     } else {
@@ -926,15 +958,15 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
 
 // Relocation at the boundary reached by advance (face / target of `a`).
 // spawn: set when a radius-derivative secondary was created into *S.
-template <typename R, bool GRAD, int WHERE = kAny>
+template <typename R, bool GRAD, int OPT, int WHERE = kAny>
 __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
-                     unsigned long long* cnt, int face, int target, Particle<R>* S, bool* spawn) {
+                     unsigned* cnt, int face, int target, Particle<R>* S, bool* spawn) {
   cnt[C_CROSS]++;
   if (WHERE == kInPrim || (WHERE == kAny && P.vol >= 0)) {
     // leave the current primitive: EXIT scorers, then relocate
     const int from = P.vol;
     const DPrim<R>& pf = V.prims[from];
-    if (pf.exit_mask) score<R, GRAD>(kp, V, P, (unsigned)pf.exit_mask, face);
+    if (pf.exit_mask) score<R, GRAD, OPT>(kp, V, P, (unsigned)pf.exit_mask, face);
     const R e = nudge_len(P.x);
     R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
     const int v = locate_after(kp, V, dR, xn, from);
@@ -950,25 +982,25 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     }
     P.x[0] = xn[0]; P.x[1] = xn[1]; P.x[2] = xn[2];
     if (v == -2) {
-      if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
+      if (kp.world_exit_mask) score<R, GRAD, OPT>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
       return END_ESCAPED;
     }
     P.vol = v;
     if (v >= 0) {
       const DPrim<R>& pt = V.prims[v];
-      if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, -1);
+      if (pt.entry_mask) score<R, GRAD, OPT>(kp, V, P, (unsigned)pt.entry_mask, -1);
       if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
       if (pt.role == TP_ROLE_BLACK) return END_BLACK;
-      if ((pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
+      if ((OPT & kOptFull) && (pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
     }
     return -1;
   }
   if (target == -3) {
-    if (kp.world_exit_mask) score<R, GRAD>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
+    if (kp.world_exit_mask) score<R, GRAD, OPT>(kp, V, P, (unsigned)kp.world_exit_mask, -1);
     return END_ESCAPED;
   }
   const DPrim<R>& pt = V.prims[target];
-  if (pt.mirror >= 0) {
+  if ((OPT & kOptFull) && pt.mirror >= 0) {
     // supermirror: weight R(Q), specular reflection (Eq. eMirrowNewDir)
     R n[3];
     normal(pt, P.x, face, n);
@@ -999,17 +1031,17 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
   for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
   P.vol = target;
   P.last = (P.last & kStuckMask) | kNoPrim;
-  if (pt.entry_mask) score<R, GRAD>(kp, V, P, (unsigned)pt.entry_mask, face);
+  if (pt.entry_mask) score<R, GRAD, OPT>(kp, V, P, (unsigned)pt.entry_mask, face);
   if (pt.role == TP_ROLE_DETECTOR) return END_DETECTED;
   if (pt.role == TP_ROLE_BLACK) return END_BLACK;
-  if ((pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
+  if ((OPT & kOptFull) && (pt.flags & F_CHOPPER) && !chopper_open(V, pt, P)) return END_BLACK;
   return -1;
 }
 
 // Interaction at the point reached by advance: process j with probability
 // g_j Sigma_j / Sigma_g, weight / g_j, then absorption or a new direction.
 template <typename R, bool GRAD>
-__device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, unsigned long long* cnt,
+__device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, unsigned* cnt,
                        const uint4 r0, const R sig[TP_NPROC], R sig_g) {
   cnt[C_COLL]++;
   const int mat = V.prims[P.vol].material;
@@ -1057,7 +1089,7 @@ __device__ int collide(const KParams<R>& kp, const View<R>& V, Particle<R>& P, u
 // sections are recomputed from the neutron's state (event k is unchanged).
 template <typename R, bool GRAD>
 __device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar],
-                             unsigned long long* cnt) {
+                             unsigned* cnt) {
   const uint4 r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
   R sig[TP_NPROC];
   const int mat = V.prims[P.vol].material;
@@ -1068,12 +1100,12 @@ __device__ int collide_again(const KParams<R>& kp, const View<R>& V, Particle<R>
 }
 
 // One whole event (history-based kernel).
-template <typename R, bool GRAD, bool GRID>
+template <typename R, bool GRAD, int OPT>
 __device__ int step(const KParams<R>& kp, const View<R>& V, Particle<R>& P, const R (&ip)[kMaxPar], R dR,
-                    unsigned long long* cnt, Particle<R>* S, bool* spawn) {
+                    unsigned* cnt, Particle<R>* S, bool* spawn) {
   Adv<R> a;
-  const int r = advance<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, a);
-  if (r == kOutCross) return cross<R, GRAD>(kp, V, P, ip, dR, cnt, a.face, a.target, S, spawn);
+  const int r = advance<R, GRAD, OPT>(kp, V, P, ip, dR, cnt, a);
+  if (r == kOutCross) return cross<R, GRAD, OPT>(kp, V, P, ip, dR, cnt, a.face, a.target, S, spawn);
   if (r == kOutColl) return collide<R, GRAD>(kp, V, P, cnt, a.r0, a.sig, a.sig_g);
   return r;
 }
@@ -1185,7 +1217,7 @@ __device__ __forceinline__ bool sec_push(const KParams<R>& kp, const Particle<R>
   return true;
 }
 
-template <typename R, bool GRAD, bool GRID, int MINB>
+template <typename R, bool GRAD, int OPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
@@ -1209,7 +1241,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
 
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned long long cnt[kNumCounters];
+  unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
 
@@ -1258,7 +1290,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
         dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
         cnt[C_HIST]++;
         int end = -1;
-        alive = source(kp, V, P, dR, &end);
+        alive = source<R, OPT>(kp, V, P, dR, &end);
         if (!alive) {
           if (end == END_LOST) cnt[C_LOST]++;
           finish(kp, P, end);
@@ -1270,7 +1302,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
     if (__all_sync(kFull, done)) break;
     if (alive) {
       bool spawn = false;
-      const int end = step<R, GRAD, GRID>(kp, V, P, ip, dR, cnt, &S, &spawn);
+      const int end = step<R, GRAD, OPT>(kp, V, P, ip, dR, cnt, &S, &spawn);
       if (end >= 0) finish(kp, P, end);
       if (GRAD && spawn && sec_push(kp, S)) spawn = false;
       if (GRAD && spawn) {
@@ -1332,9 +1364,9 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
 
 // A new history with global index g into `slot`.  Returns -1 if it ended at
 // the source, else 1 if it starts inside a primitive, 0 in the world region.
-template <typename R>
+template <typename R, int OPT>
 __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V, Particle<R>* bank, int* pend,
-                                          int slot, unsigned long long g, unsigned long long* cnt) {
+                                          int slot, unsigned long long g, unsigned* cnt) {
   if (kp.sec_mode == 2) {   // a queued secondary: it starts where it was made
     const Particle<R> S = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[g];
     bank[slot] = S;
@@ -1354,7 +1386,7 @@ __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V
   load_params(kp, P.inst, ip, &dR);
   cnt[C_HIST]++;
   int end = -1;
-  if (!source(kp, V, P, dR, &end)) {
+  if (!source<R, OPT>(kp, V, P, dR, &end)) {
     if (end == END_LOST) cnt[C_LOST]++;
     finish(kp, P, end);
     return -1;
@@ -1367,10 +1399,10 @@ __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V
 // Advance the neutron of `slot` and, if it reaches a boundary, cross it (inside
 // a primitive every crossing is an exit, in the world region an entry; the
 // caller knows which: in_prim).  Returns true if it now waits for a collision.
-template <typename R, bool GRAD, bool GRID>
+template <typename R, bool GRAD, int OPT>
 __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
                                              Particle<R>* park, int* pend, int* parked, int slot, bool in_prim,
-                                             unsigned long long* cnt) {
+                                             unsigned* cnt) {
   Particle<R> P = bank[slot];
   R ip[kMaxPar], dR;
   load_params(kp, P.inst, ip, &dR);
@@ -1379,11 +1411,11 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
   Particle<R> S;
   int end;
   if (in_prim) {
-    end = advance<R, GRAD, GRID, kInPrim>(kp, V, P, ip, dR, cnt, a);
-    if (end == kOutCross) end = cross<R, GRAD, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+    end = advance<R, GRAD, OPT, kInPrim>(kp, V, P, ip, dR, cnt, a);
+    if (end == kOutCross) end = cross<R, GRAD, OPT, kInPrim>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
   } else {
-    end = advance<R, GRAD, GRID, kInWorld>(kp, V, P, ip, dR, cnt, a);
-    if (end == kOutCross) end = cross<R, GRAD, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
+    end = advance<R, GRAD, OPT, kInWorld>(kp, V, P, ip, dR, cnt, a);
+    if (end == kOutCross) end = cross<R, GRAD, OPT, kInWorld>(kp, V, P, ip, dR, cnt, a.face, a.target, &S, &spawn);
   }
   if (end == kOutColl) {
     pend[slot] = EV_COLL;
@@ -1410,7 +1442,7 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
 template <typename R, bool GRAD>
 __device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
                                              Particle<R>* park, int* pend, int* parked, int slot,
-                                             unsigned long long* cnt) {
+                                             unsigned* cnt) {
   Particle<R> P = bank[slot];
   R ip[kMaxPar], dR;
   load_params(kp, P.inst, ip, &dR);
@@ -1426,7 +1458,7 @@ __device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>
 }
 
 
-template <typename R, bool GRAD, bool GRID, int MINB>
+template <typename R, bool GRAD, int OPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
@@ -1462,7 +1494,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
   unsigned short* qlist = reinterpret_cast<unsigned short*>(parked + NB);  // [kNumQ][NB]
 
   const unsigned long long total = work_total(kp);
-  unsigned long long cnt[kNumCounters];
+  unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
   const int lane = tid & 31;
@@ -1505,7 +1537,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         if (tid < n_empty) {
           slot = qlist[Q_EMPTY * NB + tid];
           const unsigned long long g = claim_base + tid;
-          if (g < total) born = slot_start(kp, V, bank, pend, slot, g, cnt);
+          if (g < total) born = slot_start<R, OPT>(kp, V, bank, pend, slot, g, cnt);
         }
         q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], born == 1, slot);
         q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], born == 0, slot);
@@ -1520,7 +1552,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         bool coll = false;
         if (tid < n) {
           slot = qlist[(pass == 0 ? Q_ADVP : Q_ADVW) * NB + tid];
-          coll = slot_advance<R, GRAD, GRID>(kp, V, bank, park, pend, parked, slot, pass == 0, cnt);
+          coll = slot_advance<R, GRAD, OPT>(kp, V, bank, park, pend, parked, slot, pass == 0, cnt);
         }
         q_push(qlist + Q_COLL * NB, &qc[Q_COLL], coll, slot);
       }
@@ -1554,7 +1586,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       int t = tid;
       if (t < nA + nW) {
         const bool in_prim = t < nA;
-        slot_advance<R, GRAD, GRID>(kp, V, bank, park, pend, parked,
+        slot_advance<R, GRAD, OPT>(kp, V, bank, park, pend, parked,
                                     in_prim ? qlist[Q_ADVP * NB + t] : qlist[Q_ADVW * NB + t - nA], in_prim, cnt);
       } else if ((t -= nA + nW) < nC) {
         slot_collide<R, GRAD>(kp, V, bank, park, pend, parked, qlist[Q_COLL * NB + t], cnt);
@@ -1570,7 +1602,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         if (lane == leader) g = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
         g = __shfl_sync(kFull, g, leader) + __popc(m & ((1u << lane) - 1u));
         if (want) {
-          if (g < total) slot_start(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
+          if (g < total) slot_start<R, OPT>(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
           else claim_state = 1;
         }
       }
@@ -1602,7 +1634,7 @@ constexpr int kPool = TP_POOL;            // neutrons per warp (a multiple of 32
 static_assert(kPool % 32 == 0, "pool size");
 constexpr int kPoolGroups = kPool / 32;   // pool slots per lane
 
-template <typename R, bool GRAD, bool GRID, int MINB>
+template <typename R, bool GRAD, int OPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
@@ -1636,7 +1668,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
   int* parked = pend + kPool;
 
   const unsigned long long total = work_total(kp);
-  unsigned long long cnt[kNumCounters];
+  unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
 #pragma unroll
@@ -1708,12 +1740,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
         }
         const int avail = (int)min((unsigned long long)(n - taken), chunk_end - chunk_next);
         if (lane >= taken && lane < taken + avail)
-          slot_start(kp, V, pool, pend, slot, chunk_next + (lane - taken), cnt);
+          slot_start<R, OPT>(kp, V, pool, pend, slot, chunk_next + (lane - taken), cnt);
         chunk_next += avail;
         taken += avail;
       }
     } else if (q == Q_ADVP || q == Q_ADVW) {
-      if (slot >= 0) slot_advance<R, GRAD, GRID>(kp, V, pool, park, pend, parked, slot, q == Q_ADVP, cnt);
+      if (slot >= 0) slot_advance<R, GRAD, OPT>(kp, V, pool, park, pend, parked, slot, q == Q_ADVP, cnt);
     } else {
       if (slot >= 0) slot_collide<R, GRAD>(kp, V, pool, park, pend, parked, slot, cnt);
     }
@@ -1769,51 +1801,48 @@ __global__ void k_backward(const double* __restrict__ J, const double* __restric
 // Each kernel exists in two register budgets: 80 registers (3 blocks of 256
 // threads per SM) and, for FP32 runs, 64 registers (4 blocks; more warps to
 // hide latency, more spills).  The flag kVariantHighOcc on the variant selects
-// the second; FP64 runs always take the first.
+// the second (FP32 runs only), kVariantFull the complete feature set (else
+// the lean build, see kOptFull).
 #define TP_KERNEL_TABLE(NAME)                                                                   \
-  template <typename R, bool GRAD, bool GRID, int MINB>                                        \
+  template <typename R, bool GRAD, int OPT, int MINB>                                          \
   struct NAME##_t {                                                                            \
-    static const void* fn() { return (const void*)NAME<R, GRAD, GRID, MINB>; }                 \
+    static const void* fn() { return (const void*)NAME<R, GRAD, OPT, MINB>; }                  \
     static void launch(const KParams<R>& p, int grid, int block, size_t smem, cudaStream_t st) { \
-      NAME<R, GRAD, GRID, MINB><<<grid, block, smem, st>>>(p);                                 \
+      NAME<R, GRAD, OPT, MINB><<<grid, block, smem, st>>>(p);                                  \
     }                                                                                          \
   };
 TP_KERNEL_TABLE(k_transport)
 TP_KERNEL_TABLE(k_transport_ev)
 TP_KERNEL_TABLE(k_transport_wq)
 #undef TP_KERNEL_TABLE
-template <typename R> struct HistTag { template <bool G, bool D, int M> using k = k_transport_t<R, G, D, M>; };
-template <typename R> struct EvTag { template <bool G, bool D, int M> using k = k_transport_ev_t<R, G, D, M>; };
-template <typename R> struct WqTag { template <bool G, bool D, int M> using k = k_transport_wq_t<R, G, D, M>; };
+template <typename R> struct HistTag { template <bool G, int O, int M> using k = k_transport_t<R, G, O, M>; };
+template <typename R> struct EvTag { template <bool G, int O, int M> using k = k_transport_ev_t<R, G, O, M>; };
+template <typename R> struct WqTag { template <bool G, int O, int M> using k = k_transport_wq_t<R, G, O, M>; };
 
-// Calls F::template run<K>() with K the kernel of (variant, gradients, grid, budget).
-template <typename R, typename F>
+// Calls f(K()) with K the kernel of one family (Tag) for (options, gradients,
+// register budget).
+template <typename R, typename Tag, int OPT, typename F>
+auto with_budget(bool grad, bool hi, F&& f) {
+  if (grad && !hi) return f(typename Tag::template k<true, OPT, 3>());
+  if constexpr (sizeof(R) == 4) {
+    if (grad) return f(typename Tag::template k<true, OPT, 4>());
+    if (hi) return f(typename Tag::template k<false, OPT, 4>());
+  }
+  return f(typename Tag::template k<false, OPT, 3>());
+}
+
+template <typename R, typename Tag, typename F>
 auto with_kernel(int variant, bool grad, bool grid, F&& f) {
   const bool hi = (variant & kVariantHighOcc) && sizeof(R) == 4;
-  const int v = variant & ~kVariantHighOcc;
-  auto pick = [&](auto tag) {
-    using T = decltype(tag);
-    if (grad && !hi) return grid ? f(typename T::template k<true, true, 3>()) : f(typename T::template k<true, false, 3>());
-    if constexpr (sizeof(R) == 4) {
-      if (grad) return grid ? f(typename T::template k<true, true, 4>()) : f(typename T::template k<true, false, 4>());
-      if (hi) return grid ? f(typename T::template k<false, true, 4>()) : f(typename T::template k<false, false, 4>());
-    }
-    return grid ? f(typename T::template k<false, true, 3>()) : f(typename T::template k<false, false, 3>());
-  };
-  if (v == TP_KERNEL_WARPQ) return pick(WqTag<R>{});
-  if (v == TP_KERNEL_EVENT) return pick(EvTag<R>{});
-  return pick(HistTag<R>{});
+  const bool full = (variant & kVariantFull) != 0;
+  if (full) return grid ? with_budget<R, Tag, kOptFull | kOptGrid>(grad, hi, f) : with_budget<R, Tag, kOptFull>(grad, hi, f);
+  return grid ? with_budget<R, Tag, kOptGrid>(grad, hi, f) : with_budget<R, Tag, 0>(grad, hi, f);
 }
 
-// kernel pointer for (precision, variant, gradients, grid)
-template <typename R>
-const void* transport_fn(int variant, bool grad, bool grid) {
-  return with_kernel<R>(variant, grad, grid, [](auto k) { return decltype(k)::fn(); });
-}
-
-template <typename R>
-cudaError_t launch_any(const KParams<R>& p, int variant, bool grad, int grid, int block, size_t smem, cudaStream_t st) {
-  with_kernel<R>(variant, grad, p.use_grid != 0, [&](auto k) {
+template <typename R, typename Tag>
+cudaError_t launch_family(const KParams<R>& p, int variant, bool grad, int grid, int block, size_t smem,
+                          cudaStream_t st) {
+  with_kernel<R, Tag>(variant, grad, p.use_grid != 0, [&](auto k) {
     decltype(k)::launch(p, grid, block, smem, st);
     return 0;
   });
@@ -1834,18 +1863,84 @@ cudaError_t occupancy_of(const void* fn, int block, size_t smem, int* ctas) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
 }
 
+template <typename R, typename Tag>
+cudaError_t occupancy_family(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_of(with_kernel<R, Tag>(variant, grad, use_grid, [](auto k) { return decltype(k)::fn(); }),
+                      block, smem, ctas);
+}
+
 }  // namespace
 
-// This file is compiled twice, once per transport precision (TP_BUILD_F32 /
-// TP_BUILD_F64), so that the two halves of the kernels build in parallel.
+// This file is compiled once per (precision, kernel family) -- TP_BUILD_F32 or
+// TP_BUILD_F64 with TP_BUILD_KERNEL = 1 (history), 2 (event) or 3 (warp
+// pools) -- so that the kernels build in parallel, and once with
+// TP_BUILD_COMMON for the dispatch, the sizes and the small kernels.
+#if defined(TP_BUILD_KERNEL)
+#if TP_BUILD_KERNEL == 1
+#define TP_FAMILY HistTag
+#define TP_SUFFIX k1
+#elif TP_BUILD_KERNEL == 2
+#define TP_FAMILY EvTag
+#define TP_SUFFIX k2
+#else
+#define TP_FAMILY WqTag
+#define TP_SUFFIX k3
+#endif
+#define TP_CAT_(a, b) a##_##b
+#define TP_CAT(a, b) TP_CAT_(a, b)
 #if defined(TP_BUILD_F32)
+cudaError_t TP_CAT(launch_transport_f32, TP_SUFFIX)(const KParams<float>& p, int variant, bool grad, int grid,
+                                                     int block, size_t smem, cudaStream_t st) {
+  return launch_family<float, TP_FAMILY<float>>(p, variant, grad, grid, block, smem, st);
+}
+cudaError_t TP_CAT(occupancy_f32, TP_SUFFIX)(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_family<float, TP_FAMILY<float>>(variant, grad, use_grid, block, smem, ctas);
+}
+#endif
+#if defined(TP_BUILD_F64)
+cudaError_t TP_CAT(launch_transport_f64, TP_SUFFIX)(const KParams<double>& p, int variant, bool grad, int grid,
+                                                     int block, size_t smem, cudaStream_t st) {
+  return launch_family<double, TP_FAMILY<double>>(p, variant, grad, grid, block, smem, st);
+}
+cudaError_t TP_CAT(occupancy_f64, TP_SUFFIX)(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  return occupancy_family<double, TP_FAMILY<double>>(variant, grad, use_grid, block, smem, ctas);
+}
+#endif
+#endif  // TP_BUILD_KERNEL
+
+#if defined(TP_BUILD_COMMON)
 cudaError_t launch_transport_f32(const KParams<float>& p, int variant, bool grad, int grid, int block, size_t smem,
                                  cudaStream_t st) {
-  return launch_any(p, variant, grad, grid, block, smem, st);
+  switch (variant & 3) {
+    case TP_KERNEL_EVENT: return launch_transport_f32_k2(p, variant, grad, grid, block, smem, st);
+    case TP_KERNEL_WARPQ: return launch_transport_f32_k3(p, variant, grad, grid, block, smem, st);
+    default: return launch_transport_f32_k1(p, variant, grad, grid, block, smem, st);
+  }
+}
+
+cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block, size_t smem,
+                                 cudaStream_t st) {
+  switch (variant & 3) {
+    case TP_KERNEL_EVENT: return launch_transport_f64_k2(p, variant, grad, grid, block, smem, st);
+    case TP_KERNEL_WARPQ: return launch_transport_f64_k3(p, variant, grad, grid, block, smem, st);
+    default: return launch_transport_f64_k1(p, variant, grad, grid, block, smem, st);
+  }
 }
 
 cudaError_t occupancy_f32(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return occupancy_of(transport_fn<float>(variant, grad, use_grid), block, smem, ctas);
+  switch (variant & 3) {
+    case TP_KERNEL_EVENT: return occupancy_f32_k2(variant, grad, use_grid, block, smem, ctas);
+    case TP_KERNEL_WARPQ: return occupancy_f32_k3(variant, grad, use_grid, block, smem, ctas);
+    default: return occupancy_f32_k1(variant, grad, use_grid, block, smem, ctas);
+  }
+}
+
+cudaError_t occupancy_f64(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
+  switch (variant & 3) {
+    case TP_KERNEL_EVENT: return occupancy_f64_k2(variant, grad, use_grid, block, smem, ctas);
+    case TP_KERNEL_WARPQ: return occupancy_f64_k3(variant, grad, use_grid, block, smem, ctas);
+    default: return occupancy_f64_k1(variant, grad, use_grid, block, smem, ctas);
+  }
 }
 
 size_t particle_bytes(int precision) {
@@ -1853,7 +1948,7 @@ size_t particle_bytes(int precision) {
 }
 
 size_t bank_bytes(int variant, int precision, bool grad, int block) {
-  variant &= ~kVariantHighOcc;
+  variant &= 3;
   const size_t ps = precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
   if (variant == TP_KERNEL_EVENT)
     return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
@@ -1885,17 +1980,6 @@ cudaError_t launch_backward(const double* J, const double* grad_tallies, const d
                                                  grad_params);
   return cudaGetLastError();
 }
-#endif
-
-#if defined(TP_BUILD_F64)
-cudaError_t launch_transport_f64(const KParams<double>& p, int variant, bool grad, int grid, int block, size_t smem,
-                                 cudaStream_t st) {
-  return launch_any(p, variant, grad, grid, block, smem, st);
-}
-
-cudaError_t occupancy_f64(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return occupancy_of(transport_fn<double>(variant, grad, use_grid), block, smem, ctas);
-}
-#endif
+#endif  // TP_BUILD_COMMON
 
 }  // namespace tp

@@ -15,6 +15,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libtp.so"
 STATUS_NAMES = ["TP_OK", "TP_ERR_INVALID_ARG", "TP_ERR_GEOMETRY", "TP_ERR_CUDA", "TP_ERR_OOM",
                 "TP_ERR_TIMEOUT", "TP_ERR_STATE", "TP_ERR_ABORTED"]
 TP_TEST_SKIP_TABLE_COPY = 1
+TP_TEST_FULL_BUILD = 2
 TP_BOX, TP_TUBE, TP_SPHERE = 0, 1, 2
 TP_ROLE_BULK, TP_ROLE_DETECTOR, TP_ROLE_BLACK = 0, 1, 2
 TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3

@@ -23,11 +23,16 @@ def shard_range(n_total: int, rank: int, world: int) -> tuple[int, int]:
     return lo, hi - lo
 
 
-def step_first(step: int, rank: int, world: int, n_per_rank: int) -> int:
-    """First history id of `rank` at `step` when every rank runs n_per_rank
-    histories per step (weak scaling): steps and ranks take consecutive,
-    disjoint id ranges, so no history is repeated across steps or ranks."""
-    return (step * world + rank) * n_per_rank
+def step_stream(step: int, rank: int, world: int, n_per_rank: int, seed: int) -> tuple[int, int]:
+    """(Philox key, first history id) of `rank` at `step` when every rank runs
+    n_per_rank histories per step (weak scaling), so that no history is ever
+    repeated across steps or ranks: each step takes its own key (seed + step),
+    and within a step the ranks take consecutive id ranges while all of them
+    fit below 2^32 (history ids are 32-bit counter words); beyond that each
+    rank takes its own key as well."""
+    if world * n_per_rank <= 2 ** 32:
+        return seed + step, rank * n_per_rank
+    return seed + step * world + rank, 0
 
 
 def reduce_sums(parts: dict, group=None) -> dict:

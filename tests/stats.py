@@ -38,6 +38,25 @@ def compare_tallies(m1, e1, m2, e2, frac_3sigma=0.99, max_sigma=5.0, p_min=1e-3)
                 "lonely": int(lonely.sum())}
 
 
+def compare_tallies_unequal(m1, e1, n1, m2, e2, n2, min_count=25.0, **kw):
+    """compare_tallies for samples of very different sizes: a bin whose
+    expected count in the smaller sample (mean x n, unit weights) is below
+    min_count has no usable error estimate there, so such bins are merged
+    into one aggregate bin (sums of means and of variances) before the
+    comparison; the well-populated bins are compared one by one."""
+    m1, e1, m2, e2 = map(lambda a: np.asarray(a, dtype=np.float64), (m1, e1, m2, e2))
+    nmin = float(min(n1, n2))
+    big = 0.5 * (np.abs(m1) + np.abs(m2)) * nmin >= min_count
+    rest = ~big
+    agg = lambda a: np.array([a[rest].sum()])
+    aggs = lambda a: np.array([math.sqrt((a[rest] ** 2).sum())])
+    M1 = np.concatenate([m1[big], agg(m1)]); E1 = np.concatenate([e1[big], aggs(e1)])
+    M2 = np.concatenate([m2[big], agg(m2)]); E2 = np.concatenate([e2[big], aggs(e2)])
+    ok, info = compare_tallies(M1, E1, M2, E2, **kw)
+    info["merged_bins"] = int(rest.sum())
+    return ok, info
+
+
 def chi2_sf(x, k):
     """Upper tail of the chi-square distribution (Wilson-Hilferty for large k)."""
     try:

@@ -82,16 +82,17 @@ def test_shard_ranges_partition_the_ids():
         shard.shard_range(10, 2, 2)
 
 
-def test_step_ids_never_repeat():
-    world, n = 4, 1000
+@pytest.mark.parametrize("world,n", [(4, 1000), (8, 1_000_000_000)])
+def test_step_streams_never_repeat_a_history(world, n):
     seen = set()
     for step in range(5):
         for r in range(world):
-            f = shard.step_first(step, r, world, n)
-            span = set(range(f, f + n))
-            assert not (span & seen)
-            seen |= span
-    assert seen == set(range(5 * world * n))
+            key, first = shard.step_stream(step, r, world, n, seed=4096)
+            assert first + n <= 2 ** 32
+            span = (key, first, first + n)
+            for k2, a, b in seen:
+                assert k2 != key or b <= first or first + n <= a, (span, (k2, a, b))
+            seen.add(span)
 
 
 def test_reduce_sums_rejects_reduced_precision():
