@@ -262,7 +262,12 @@ typedef struct {
  *   secondaries fit the queue (at most 2^25 records, sized at the first such
  *   run; a secondary finding the queue full is transported in place); 0 =
  *   chosen by the autotuner with kernel 0, else 1.  Results do not depend on
- *   the choice (each secondary has its own random numbers). */
+ *   the choice (each secondary has its own random numbers).
+ * regroup (event kernel, plain runs): the bank is regrouped every `regroup`
+ *   events -- sorted into sub-queues by event type, primitive shape and
+ *   material, so that a warp runs one kind of event -- and in between each
+ *   thread runs the next events of the neutron it holds; 0 = chosen by the
+ *   autotuner with kernel 0 (1 or 4), else 1.  Results do not depend on it. */
 typedef struct {
   uint64_t seed;
   const uint64_t* n_histories;
@@ -276,6 +281,7 @@ typedef struct {
   int kernel;
   int use_graph;
   int secondaries;
+  int regroup;
 } tp_run;
 
 enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2, TP_KERNEL_WARPQ = 3 };
@@ -355,8 +361,10 @@ tp_status tp_abort(tp_scene* s);
  * returns with nothing in flight and nothing transported.  s = NULL sets the
  * flags of tp_run_histories_noalloc, which has no scene.
  * TP_TEST_FULL_BUILD: the scene runs the kernels' complete feature build even
- * if the lean one serves it (the two must agree; the test of that uses it). */
-enum { TP_TEST_SKIP_TABLE_COPY = 1, TP_TEST_FULL_BUILD = 2 };
+ * if the lean one serves it (the two must agree; the test of that uses it).
+ * TP_TEST_SMALL_SEC_QUEUE: the queue of radius-derivative secondaries holds at
+ * most 2^20 records, so that a short run goes through several chunks. */
+enum { TP_TEST_SKIP_TABLE_COPY = 1, TP_TEST_FULL_BUILD = 2, TP_TEST_SMALL_SEC_QUEUE = 4 };
 tp_status tp_set_test_flags(tp_scene* s, int flags);
 
 /* Launch configuration of the last run: kernel (TP_KERNEL_*), block size and
@@ -388,7 +396,7 @@ int tp_total_bins(const tp_scene* s);
  *    read as in tp_create_scene, tp_set_materials, tp_set_bias and
  *    tp_run_histories, with these restrictions (TP_ERR_INVALID_ARG
  *    otherwise): r->want_grad, r->records, r->use_graph and r->secondaries
- *    must be 0/NULL, and r->kernel 0 or TP_KERNEL_HISTORY: the call always
+ *    must be 0/NULL, r->regroup 0 or 1, and r->kernel 0 or TP_KERNEL_HISTORY: the call always
  *    runs the history-based kernel with the tables staged when they fit, and
  *    builds no uniform grid, so a scene of many primitives tests all of them
  *    at every step of the world region (same results, more work).

@@ -102,6 +102,7 @@ struct LaunchCfg {
   int hi;      // the 64-register build (FP32 runs only)
   int defer;   // gradient runs: secondaries queued and transported in a second pass
   int full = 1;  // the build with every feature (else the lean one)
+  int regroup = 1;  // event kernel, plain runs: events between regroupings
   int variant() const { return kernel | (hi ? kVariantHighOcc : 0) | (full ? kVariantFull : 0); }
 };
 
@@ -166,6 +167,7 @@ struct tp_scene {
   int smem_optin = 0; // shared memory a block may use on this device (queried once)
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
   int tuned_defer = 0;   // gradient runs: secondaries queued for a second pass
+  int tuned_regroup[2] = {1, 1};   // event kernel: events between regroupings
   // queue of radius-derivative secondaries for the second pass (gradient runs)
   uint8_t* d_sec = nullptr;
   unsigned long long* d_sec_count = nullptr;
@@ -572,6 +574,9 @@ tp_status upload_blob(tp_scene* s) {
 }
 
 constexpr uint32_t kMaxStagedBlob = 96 * 1024;  // larger tables are read through L1/L2
+// The sparse regrouping interval the autotuner tries beside regrouping every
+// event (event kernel, plain runs).
+constexpr int kRegroupSparse = 4;
 
 template <typename R>
 void fill_common(const tp_scene* s, KParams<R>& k) {
@@ -724,6 +729,7 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
   k.n_records = records ? n_records : 0;
   k.sum = o.sum; k.sumsq = o.sumsq; k.J = o.J; k.J2 = o.J2; k.counters = o.counters;
   k.stage_blob = c.stage;
+  k.regroup = c.regroup;
   const int grid = s->sm_count * c.ctas;
   const long long warps = (long long)grid * (c.block / 32);
   k.chunk = sec_mode == 2 ? 16 : (int)std::max(1ll, std::min(256ll, (long long)(total / (unsigned long long)(warps * 8))));
@@ -735,21 +741,27 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
 }
 
 // Histories a chunk of a queued-secondaries run may hold: the queue takes
-// kSecPerHistory secondaries per history (about twice what the densest
-// workloads make); a fuller queue transports the rest in place.
-constexpr unsigned long long kSecPerHistory = 8;
-constexpr unsigned long long kSecCapMin = 1ull << 16, kSecCapMax = 1ull << 25;
+// kSecPerHistory secondaries per history (the batched powder workload makes
+// 3.5 on average); a fuller queue transports the rest in place.  Records are
+// 56 bytes in FP32, so the largest queue (2^28) holds 15 GB.
+constexpr unsigned long long kSecPerHistory = 6;
+constexpr unsigned long long kSecCapMin = 1ull << 16, kSecCapMax = 1ull << 28;
 
 // The queue of secondaries for runs of up to `total` histories (allocated
 // outside any stream capture; a larger one drops the captured graph).
 tp_status ensure_sec(tp_scene* s, unsigned long long total) {
+  // at most a quarter of the free device memory
+  size_t free_b = 0, total_b = 0;
+  TP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const unsigned long long mem_cap = (unsigned long long)(free_b / 4 / particle_bytes(s->precision));
+  const unsigned long long cap = (s->test_flags & TP_TEST_SMALL_SEC_QUEUE) ? (1ull << 20) : kSecCapMax;
   unsigned long long want = kSecCapMin;
-  while (want < kSecCapMax && want < kSecPerHistory * total) want <<= 1;
+  while (want < cap && want < kSecPerHistory * total && 2 * want <= mem_cap) want <<= 1;
   if (s->sec_cfg.kernel == 0) {
     tp_status st = resolve(s, false, TP_KERNEL_WARPQ, 256, 0, &s->sec_cfg, -1, s->precision == TP_FP32 ? 1 : 0);
     if (st != TP_OK) return st;
   }
-  if (s->d_sec && s->sec_cap >= want) return TP_OK;
+  if (s->d_sec && s->sec_cap >= want && s->sec_cap <= cap) return TP_OK;
   if (s->stage_pending) { TP_CUDA(cudaEventSynchronize(s->stage_done)); s->stage_pending = false; }
   TP_CUDA(cudaDeviceSynchronize());
   cudaFree(s->d_sec);
@@ -818,6 +830,10 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
       cfg.defer = 1;
       cfgs.push_back(cfg);
     }
+    if (!grad && c[0] == TP_KERNEL_EVENT) {   // and regrouped every kRegroupSparse events
+      cfg.regroup = kRegroupSparse;
+      cfgs.push_back(cfg);
+    }
   }
   if (cfgs.empty()) {
     cudaFree(scratch);
@@ -863,6 +879,7 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
   s->tuned_block[grad] = pick.block;
   s->tuned_stage[grad] = pick.stage;
   s->tuned_hi[grad] = pick.hi;
+  s->tuned_regroup[grad] = pick.regroup;
   if (grad) s->tuned_defer = pick.defer;
   return TP_OK;
 }
@@ -874,7 +891,8 @@ tp_status autotune(tp_scene* s, bool grad, uint64_t seed, unsigned long long tot
 tp_status run_graph(tp_scene* s, const LaunchCfg& cfg, bool grad, const tp_run* r, unsigned long long total,
                     const Outputs& o, cudaStream_t st) {
   const unsigned long long key[8] = {(unsigned long long)cfg.variant(), (unsigned long long)cfg.block,
-                                     (unsigned long long)(cfg.ctas * 4 + cfg.stage * 2 + cfg.defer), (unsigned long long)grad,
+                                     (unsigned long long)(cfg.ctas * 256 + cfg.regroup * 4 + cfg.stage * 2 + cfg.defer),
+                                     (unsigned long long)grad,
                                      r->seed, total,
                                      (unsigned long long)(uintptr_t)r->records, r->records ? r->n_records : 0};
   if (!s->graph || std::memcmp(key, s->graph_key, sizeof key) != 0) {
@@ -1239,6 +1257,8 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
                         r->kernel == TP_KERNEL_AUTO && r->ctas_per_sm == 0 ? s->tuned_hi[grad] : -1);
   if (e != TP_OK) return e;
   if (grad) cfg.defer = r->secondaries == 2 || (r->secondaries == 0 && r->kernel == TP_KERNEL_AUTO && s->tuned_defer);
+  if (r->regroup < 0 || r->regroup > 64) return fail(TP_ERR_INVALID_ARG, "regroup %d: need 0..64", r->regroup);
+  cfg.regroup = r->regroup > 0 ? r->regroup : (r->kernel == TP_KERNEL_AUTO ? s->tuned_regroup[grad] : 1);
   Outputs o{s->d_sum, s->d_sumsq, s->d_J, s->d_J2, s->d_counters};
   if (r->use_graph) {
     e = run_graph(s, cfg, grad, r, total, o, st);
@@ -1383,7 +1403,7 @@ tp_status tp_abort(tp_scene* s) {
 
 tp_status tp_set_test_flags(tp_scene* s, int flags) {
   g_err.clear();
-  if (flags & ~(TP_TEST_SKIP_TABLE_COPY | TP_TEST_FULL_BUILD))
+  if (flags & ~(TP_TEST_SKIP_TABLE_COPY | TP_TEST_FULL_BUILD | TP_TEST_SMALL_SEC_QUEUE))
     return fail(TP_ERR_INVALID_ARG, "unknown test flags %#x", flags);
   if (!s) {
     g_noalloc_test_flags.store(flags & TP_TEST_SKIP_TABLE_COPY);
@@ -1478,8 +1498,8 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   if (r->want_grad || r->records) return fail(TP_ERR_INVALID_ARG, "no gradients or records in the allocation-free call");
   if (r->kernel != TP_KERNEL_AUTO && r->kernel != TP_KERNEL_HISTORY)
     return fail(TP_ERR_INVALID_ARG, "kernel %d: the allocation-free call runs the history kernel only", r->kernel);
-  if (r->use_graph || r->secondaries)
-    return fail(TP_ERR_INVALID_ARG, "the allocation-free call takes no graph or secondaries option");
+  if (r->use_graph || r->secondaries || r->regroup > 1)
+    return fail(TP_ERR_INVALID_ARG, "the allocation-free call takes no graph, secondaries or regroup option");
   if (d->n_instances < 1 || d->n_instances > TP_NOALLOC_MAX_INSTANCES)
     return fail(TP_ERR_INVALID_ARG, "n_instances %d: the allocation-free call takes 1..%d", d->n_instances,
                 TP_NOALLOC_MAX_INSTANCES);

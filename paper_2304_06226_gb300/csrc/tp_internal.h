@@ -112,6 +112,9 @@ struct KParams {
   unsigned long long total;
   unsigned long long* work_counter;
   int chunk;  // histories a warp claims at once
+  // event kernel, plain runs: the bank is regrouped every `regroup` events
+  // (1 = every event); in between, each thread continues its own neutron
+  int regroup;
   unsigned long long index_base;  // global index of claim 0 (one chunk of a longer run)
   // Radius-derivative secondaries of gradient runs: 0 = transported where
   // they are made; 1 = appended to sec_buf (transported in place only when it

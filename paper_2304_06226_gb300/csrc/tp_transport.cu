@@ -29,7 +29,10 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <cstddef>
 #include <cstdint>
+#include <cstring>
+#include <type_traits>
 
 #include "tp_internal.h"
 
@@ -97,7 +100,10 @@ __device__ __forceinline__ double d_atan2(double y, double x) { return atan2(y, 
 // ---------------------------------------------------------------------------
 // Philox4x32-10
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+// Out of line: the block is drawn at several places of the event loop, and
+// one shared copy keeps the loop's instruction footprint smaller (measured
+// faster than inlining every copy).
+__device__ __noinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
     const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
@@ -116,11 +122,16 @@ template <typename R>
 struct Particle {
   R x[3], u[3];
   R lam, w;
-  R A[kMaxPar];
   R s;       // path length flown since the source (time of flight s lam / kHoverMn)
   int vol, nscat;
-  uint32_t k, hid, inst, sub0, nsec;  // sub0 != 0: a radius-derivative secondary
+  uint32_t k, hid, inst;
   int last;  // primitive just left, flags and stuck count (see kNoPrim)
+  // sub0 != 0 marks a radius-derivative secondary (the plain second pass of
+  // gradient runs transports them), nsec counts the secondaries made
+  uint32_t sub0, nsec;
+  // gradient runs only (zero in plain runs, whose shared-memory banks keep
+  // just the fields above): the score-function accumulators
+  R A[kMaxPar];
 };
 
 template <typename R>
@@ -133,6 +144,46 @@ struct View {
   const R* line_d;
   const R* line_cum;
   const int* nb;
+};
+
+// Neutron bank in shared memory as a structure of arrays: the neutron state
+// is a sequence of words (32-bit in FP32, 64-bit in FP64) and word i of the
+// neutron in slot s lives at w[i * n + s], so that a warp touching the same
+// field of different slots reads consecutive words.  Plain runs (GRAD false)
+// keep only the words before Particle::A -- the accumulators are zero there --
+// which shrinks the bank by a fifth.
+template <typename R, bool GRAD>
+struct Bank {
+  using Word = typename std::conditional<sizeof(R) == 8, unsigned long long, unsigned>::type;
+  static constexpr size_t kBytes = GRAD ? sizeof(Particle<R>) : offsetof(Particle<R>, A);
+  static constexpr int kWords = (int)(kBytes / sizeof(Word));
+  static_assert(kBytes % sizeof(Word) == 0 && sizeof(Particle<R>) % sizeof(Word) == 0, "whole words");
+  Word* w;
+  int n;   // slots
+  __device__ __forceinline__ Bank(void* base, int nslots) : w(static_cast<Word*>(base)), n(nslots) {}
+  __device__ __forceinline__ Particle<R> load(int s) const {
+    Word t[sizeof(Particle<R>) / sizeof(Word)];
+#pragma unroll
+    for (int i = 0; i < kWords; ++i) t[i] = w[i * n + s];
+#pragma unroll
+    for (int i = kWords; i < (int)(sizeof(Particle<R>) / sizeof(Word)); ++i) t[i] = 0;
+    Particle<R> P;
+    memcpy(&P, t, sizeof P);
+    return P;
+  }
+  __device__ __forceinline__ void store(int s, const Particle<R>& P) const {
+    Word t[sizeof(Particle<R>) / sizeof(Word)];
+    memcpy(t, &P, sizeof P);
+#pragma unroll
+    for (int i = 0; i < kWords; ++i) w[i * n + s] = t[i];
+  }
+  // the volume field alone (the regrouping reads it to sort advances)
+  __device__ __forceinline__ int vol(int s) const {
+    constexpr size_t off = offsetof(Particle<R>, vol);
+    const Word* word = w + (off / sizeof(Word)) * n + s;
+    return reinterpret_cast<const int*>(word)[(off % sizeof(Word)) / sizeof(int)];
+  }
+  static __host__ __device__ constexpr size_t bytes(int nslots) { return kBytes * (size_t)nslots; }
 };
 
 // Register arrays are only indexed with compile-time indices (a runtime index
@@ -1171,11 +1222,15 @@ __device__ bool stage_tables(uint8_t* dst, const uint8_t* src, uint32_t bytes, u
   return __syncthreads_and(ok) != 0;
 }
 
-// Host-requested stop (tp_abort): checked whenever new histories are claimed.
-// Records TP_ERR_ABORTED (unless an earlier error is recorded) and returns true.
+// Host-requested stop (tp_abort).  The flag lives in mapped host memory,
+// whose reads take microseconds, so a thread reads it at its first claim of
+// new histories and then at every kAbortPollEvery-th one; returns true (and
+// records TP_ERR_ABORTED unless an earlier error is recorded) once it is set.
+constexpr unsigned kAbortPollEvery = 32;
+
 template <typename R>
-__device__ __forceinline__ bool aborted(const KParams<R>& kp) {
-  if (!kp.abort_flag || *kp.abort_flag == 0) return false;
+__device__ __forceinline__ bool aborted(const KParams<R>& kp, unsigned& polls) {
+  if (!kp.abort_flag || (polls++ % kAbortPollEvery) != 0 || *kp.abort_flag == 0) return false;
   atomicCAS(kp.status, 0, (int)TP_ERR_ABORTED);
   return true;
 }
@@ -1198,6 +1253,41 @@ __device__ __forceinline__ void finish(const KParams<R>& kp, const Particle<R>& 
   }
 }
 
+// A queued radius-derivative secondary (second pass of gradient runs): the
+// state it starts from.  A secondary carries no score-function accumulators
+// (it scores its weight into the radius tallies only), makes no secondaries,
+// and starts at event 0 next to no primitive, so 14 words hold it.
+template <typename R>
+struct SecRec {
+  R x[3], u[3], lam, w, s;
+  int vol, nscat;
+  uint32_t hid, inst, sub0;
+};
+
+template <typename R>
+__device__ __forceinline__ void sec_write(SecRec<R>* q, const Particle<R>& S) {
+  SecRec<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { r.x[i] = S.x[i]; r.u[i] = S.u[i]; }
+  r.lam = S.lam; r.w = S.w; r.s = S.s;
+  r.vol = S.vol; r.nscat = S.nscat; r.hid = S.hid; r.inst = S.inst; r.sub0 = S.sub0;
+  *q = r;
+}
+
+template <typename R>
+__device__ __forceinline__ Particle<R> sec_read(const SecRec<R>* q) {
+  const SecRec<R> r = *q;
+  Particle<R> P;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { P.x[i] = r.x[i]; P.u[i] = r.u[i]; }
+  P.lam = r.lam; P.w = r.w; P.s = r.s;
+#pragma unroll
+  for (int i = 0; i < kMaxPar; ++i) P.A[i] = R(0);
+  P.vol = r.vol; P.nscat = r.nscat; P.hid = r.hid; P.inst = r.inst; P.sub0 = r.sub0;
+  P.k = 0; P.nsec = 0; P.last = kNoPrim;
+  return P;
+}
+
 // Histories (or queued secondaries) a launch works through.
 template <typename R>
 __device__ __forceinline__ unsigned long long work_total(const KParams<R>& kp) {
@@ -1208,12 +1298,14 @@ __device__ __forceinline__ unsigned long long work_total(const KParams<R>& kp) {
 
 // Appends a radius-derivative secondary to the queue of the second pass;
 // false if the queue is full (the caller then transports it in place).
+// One atomic per record: the lanes that push are in divergent code, where no
+// warp-wide aggregation is safe.
 template <typename R>
 __device__ __forceinline__ bool sec_push(const KParams<R>& kp, const Particle<R>& S) {
   if (kp.sec_mode != 1) return false;
   const unsigned long long i = atomicAdd(kp.sec_count, 1ull);
   if (i >= kp.sec_cap) return false;
-  reinterpret_cast<Particle<R>*>(kp.sec_buf)[i] = S;
+  sec_write(reinterpret_cast<SecRec<R>*>(kp.sec_buf) + i, S);
   return true;
 }
 
@@ -1244,6 +1336,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
   unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+  unsigned polls = 0;   // claims made by this thread (abort polling)
 
   Particle<R> P, park, S;
   R ip[kMaxPar];
@@ -1258,7 +1351,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
     while (idle) {
       if (chunk_next >= chunk_end) {
         unsigned long long b = 0;
-        if (lane == 0) b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+        if (lane == 0) b = aborted(kp, polls) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
         b = __shfl_sync(kFull, b, 0);
         if (b >= total) {
           if (!alive) done = true;
@@ -1270,7 +1363,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
       const unsigned avail = (unsigned)min((unsigned long long)__popc(idle), chunk_end - chunk_next);
       const unsigned rank = __popc(idle & lt_mask);
       if (((idle >> lane) & 1u) && rank < avail && kp.sec_mode == 2) {
-        P = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[chunk_next + rank];   // a queued secondary
+        P = sec_read(reinterpret_cast<const SecRec<R>*>(kp.sec_buf) + chunk_next + rank);   // a queued secondary
 #pragma unroll
         for (int i = 0; i < kMaxPar; ++i) ip[i] = __ldg(kp.inst_params + (size_t)P.inst * kMaxPar + i);
         dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
@@ -1337,6 +1430,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(const __grid_constant__
 // ---------------------------------------------------------------------------
 enum { EV_EMPTY = 0, EV_ADV = 1, EV_COLL = 2 };
 enum { Q_EMPTY = 0, Q_ADVP, Q_ADVW, Q_COLL, kNumQ };
+// plain runs: the queues concatenated in this order
+enum { QP_ADVP = 0, QP_ADVW, QP_COLL, QP_EMPTY, kNumQPlain };
+constexpr int kNumQMax = kNumQPlain > kNumQ ? kNumQPlain : kNumQ;
 
 // Append `slot` to queue q if `pred`; all lanes of the warp must call this.
 __device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pred, int slot) {
@@ -1364,12 +1460,12 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
 
 // A new history with global index g into `slot`.  Returns -1 if it ended at
 // the source, else 1 if it starts inside a primitive, 0 in the world region.
-template <typename R, int OPT>
-__device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V, Particle<R>* bank, int* pend,
+template <typename R, bool GRAD, int OPT>
+__device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V, const Bank<R, GRAD>& bank, int* pend,
                                           int slot, unsigned long long g, unsigned* cnt) {
   if (kp.sec_mode == 2) {   // a queued secondary: it starts where it was made
-    const Particle<R> S = reinterpret_cast<const Particle<R>*>(kp.sec_buf)[g];
-    bank[slot] = S;
+    const Particle<R> S = sec_read(reinterpret_cast<const SecRec<R>*>(kp.sec_buf) + g);
+    bank.store(slot, S);
     pend[slot] = EV_ADV;
     return S.vol >= 0 ? 1 : 0;
   }
@@ -1391,7 +1487,7 @@ __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V
     finish(kp, P, end);
     return -1;
   }
-  bank[slot] = P;
+  bank.store(slot, P);
   pend[slot] = EV_ADV;
   return P.vol >= 0 ? 1 : 0;
 }
@@ -1400,10 +1496,10 @@ __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V
 // a primitive every crossing is an exit, in the world region an entry; the
 // caller knows which: in_prim).  Returns true if it now waits for a collision.
 template <typename R, bool GRAD, int OPT>
-__device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
-                                             Particle<R>* park, int* pend, int* parked, int slot, bool in_prim,
+__device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>& V, const Bank<R, GRAD>& bank,
+                                             const Bank<R, GRAD>& park, int* pend, int* parked, int slot, bool in_prim,
                                              unsigned* cnt) {
-  Particle<R> P = bank[slot];
+  Particle<R> P = bank.load(slot);
   R ip[kMaxPar], dR;
   load_params(kp, P.inst, ip, &dR);
   Adv<R> a;
@@ -1424,37 +1520,37 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
     if (end >= 0) finish(kp, P, end);
     if (GRAD && spawn && sec_push(kp, S)) spawn = false;
     if (GRAD && spawn) {
-      if (end < 0) { park[slot] = P; parked[slot] = 1; }
+      if (end < 0) { park.store(slot, P); parked[slot] = 1; }
       P = S;
       pend[slot] = EV_ADV;
     } else if (end >= 0) {
-      if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+      if (GRAD && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
       else pend[slot] = EV_EMPTY;
     } else {
       pend[slot] = EV_ADV;
     }
   }
-  bank[slot] = P;
+  bank.store(slot, P);
   return coll;
 }
 
 // The collision the neutron of `slot` waits for.
 template <typename R, bool GRAD>
-__device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>& V, Particle<R>* bank,
-                                             Particle<R>* park, int* pend, int* parked, int slot,
+__device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>& V, const Bank<R, GRAD>& bank,
+                                             const Bank<R, GRAD>& park, int* pend, int* parked, int slot,
                                              unsigned* cnt) {
-  Particle<R> P = bank[slot];
+  Particle<R> P = bank.load(slot);
   R ip[kMaxPar], dR;
   load_params(kp, P.inst, ip, &dR);
   const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
   if (end >= 0) {
     finish(kp, P, end);
-    if (GRAD && parked[slot]) { P = park[slot]; parked[slot] = 0; pend[slot] = EV_ADV; }
+    if (GRAD && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
     else pend[slot] = EV_EMPTY;
   } else {
     pend[slot] = EV_ADV;
   }
-  bank[slot] = P;
+  bank.store(slot, P);
 }
 
 
@@ -1462,7 +1558,7 @@ template <typename R, bool GRAD, int OPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constant__ KParams<R> kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar;
-  __shared__ int qcount[2][kNumQ];   // per iteration parity (plain runs)
+  __shared__ int qcount[2][kNumQMax];   // per regrouping parity (plain runs)
   __shared__ unsigned long long claim_base;
   __shared__ int claim_state;        // 0 work left, 1 exhausted
   const int NB = blockDim.x;
@@ -1486,21 +1582,24 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
   V.line_d = reinterpret_cast<const R*>(base + kp.off_line_d);
   V.line_cum = reinterpret_cast<const R*>(base + kp.off_line_cum);
   V.nb = reinterpret_cast<const int*>(base + kp.off_nb);
-  // bank layout after the tables
-  Particle<R>* bank = reinterpret_cast<Particle<R>*>(smem + tab);
-  Particle<R>* park = bank + NB;                      // parked primaries (gradient runs)
-  int* pend = reinterpret_cast<int*>(park + (GRAD ? NB : 0));
+  // bank layout after the tables: the bank, parked primaries (gradient runs),
+  // pending event types, parked flags, queues
+  using BankT = Bank<R, GRAD>;
+  const BankT bank(smem + tab, NB);
+  const BankT park(smem + tab + BankT::bytes(NB), NB);
+  int* pend = reinterpret_cast<int*>(smem + tab + BankT::bytes(NB) * (GRAD ? 2 : 1));
   int* parked = pend + NB;
-  unsigned short* qlist = reinterpret_cast<unsigned short*>(parked + NB);  // [kNumQ][NB]
+  unsigned short* qlist = reinterpret_cast<unsigned short*>(parked + NB);  // [kNumQMax][NB]
 
   const unsigned long long total = work_total(kp);
   unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+  unsigned polls = 0;   // claims made by this thread (abort polling)
   const int lane = tid & 31;
   pend[tid] = EV_EMPTY;
   parked[tid] = 0;
-  if (tid < 2 * kNumQ) qcount[tid / kNumQ][tid % kNumQ] = 0;
+  if (tid < 2 * kNumQMax) qcount[tid / kNumQMax][tid % kNumQMax] = 0;
   if (tid == 0) claim_state = 0;
   __syncthreads();
 
@@ -1516,7 +1615,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       __syncthreads();
       {
         const int ty = pend[tid];
-        const bool inprim = ty == EV_ADV && bank[tid].vol >= 0;
+        const bool inprim = ty == EV_ADV && bank.vol(tid) >= 0;
         q_push(qlist + Q_EMPTY * NB, &qc[Q_EMPTY], ty == EV_EMPTY, tid);
         q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], ty == EV_ADV && inprim, tid);
         q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], ty == EV_ADV && !inprim, tid);
@@ -1526,7 +1625,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       if (tid == 0) {
         claim_base = total;
         if (n_empty > 0 && claim_state == 0) {
-          const unsigned long long b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)n_empty);
+          const unsigned long long b = aborted(kp, polls) ? total : atomicAdd(kp.work_counter, (unsigned long long)n_empty);
           claim_base = b;
           if (b + n_empty >= total) claim_state = 1;
         }
@@ -1537,7 +1636,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
         if (tid < n_empty) {
           slot = qlist[Q_EMPTY * NB + tid];
           const unsigned long long g = claim_base + tid;
-          if (g < total) born = slot_start<R, OPT>(kp, V, bank, pend, slot, g, cnt);
+          if (g < total) born = slot_start<R, GRAD, OPT>(kp, V, bank, pend, slot, g, cnt);
         }
         q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], born == 1, slot);
         q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], born == 0, slot);
@@ -1561,52 +1660,75 @@ __global__ void __launch_bounds__(256, MINB) k_transport_ev(const __grid_constan
       __syncthreads();
     }
   } else {
-    // Plain runs: one work phase per iteration in which thread t takes the
-    // t-th entry of the concatenated queues [advance in a primitive | advance
-    // in the world region | collision | refill], so that every thread of the
-    // block has a slot and each warp runs one kind of event (but those at the
-    // joins).  Two barriers per iteration; the counts alternate between two
-    // buffers so that a reset never meets a reader.
+    // Plain runs: one work phase per iteration.  In a regrouping iteration
+    // thread t takes the t-th entry of the concatenated queues [advance in a
+    // primitive | advance in the world region | collision | refill], so that
+    // every thread of the block has a slot and each warp runs one kind of
+    // event (but those at the joins).  Two barriers per regrouping; the
+    // counts alternate between two buffers so that a reset never meets a
+    // reader.  With
+    // kp.regroup = R > 1 only every R-th iteration regroups: in between, each
+    // thread runs the next event of the neutron it had, without barriers.
+    const int every = kp.regroup > 1 ? kp.regroup : 1;
+    int my_slot = -1, ri = 0;
     for (int iter = 0;; ++iter) {
-      int* qc = qcount[iter & 1];
-      bool exhausted;
-      {
-        const int ty = pend[tid];
-        const bool inprim = ty == EV_ADV && bank[tid].vol >= 0;
-        q_push(qlist + Q_ADVP * NB, &qc[Q_ADVP], ty == EV_ADV && inprim, tid);
-        q_push(qlist + Q_ADVW * NB, &qc[Q_ADVW], ty == EV_ADV && !inprim, tid);
-        q_push(qlist + Q_COLL * NB, &qc[Q_COLL], ty == EV_COLL, tid);
-        q_push(qlist + Q_EMPTY * NB, &qc[Q_EMPTY], ty == EV_EMPTY, tid);
-        if (tid < kNumQ) qcount[(iter + 1) & 1][tid] = 0;   // last read in the previous work phase
-        exhausted = claim_state != 0;                       // last written in the previous work phase
+      const bool regroup = (iter % every) == 0;
+      int slot = -1, kind = 0;   // 1 advance in a primitive, 2 in the world region, 3 collision
+      bool want = false;         // refill rslot with a new history
+      int rslot = -1;
+      if (regroup) {
+        int* qc = qcount[ri & 1];
+        bool exhausted;
+        {
+          const int ty = pend[tid];
+          const bool inprim = ty == EV_ADV && bank.vol(tid) >= 0;
+          q_push(qlist + QP_ADVP * NB, &qc[QP_ADVP], ty == EV_ADV && inprim, tid);
+          q_push(qlist + QP_ADVW * NB, &qc[QP_ADVW], ty == EV_ADV && !inprim, tid);
+          q_push(qlist + QP_COLL * NB, &qc[QP_COLL], ty == EV_COLL, tid);
+          q_push(qlist + QP_EMPTY * NB, &qc[QP_EMPTY], ty == EV_EMPTY, tid);
+          if (tid < kNumQPlain) qcount[(ri + 1) & 1][tid] = 0;   // last read in the previous regrouping
+          exhausted = claim_state != 0;                         // last written before the last barrier
+        }
+        __syncthreads();
+        int live = 0;
+#pragma unroll
+        for (int q = 0; q < QP_EMPTY; ++q) live += qc[q];
+        if (live == 0 && exhausted) break;   // uniform: shared values read before any write
+        int t = tid, q = 0;
+        for (; q < QP_EMPTY; ++q) {
+          if (t < qc[q]) break;
+          t -= qc[q];
+        }
+        if (q < QP_EMPTY) {
+          slot = qlist[q * NB + t];
+          kind = q == QP_ADVP ? 1 : (q == QP_ADVW ? 2 : 3);
+        } else if (t < qc[QP_EMPTY] && !exhausted) {
+          want = true;
+          rslot = qlist[QP_EMPTY * NB + t];
+        }
+        ++ri;
+      } else if (my_slot >= 0) {
+        const int ty = pend[my_slot];
+        if (ty == EV_ADV) { slot = my_slot; kind = bank.vol(my_slot) >= 0 ? 1 : 2; }
+        else if (ty == EV_COLL) { slot = my_slot; kind = 3; }
+        else if (claim_state == 0) { want = true; rslot = my_slot; }
       }
-      __syncthreads();
-      const int nA = qc[Q_ADVP], nW = qc[Q_ADVW], nC = qc[Q_COLL], nE = qc[Q_EMPTY];
-      if (nA + nW + nC == 0 && exhausted) break;   // uniform: shared values read before any write
-      int t = tid;
-      if (t < nA + nW) {
-        const bool in_prim = t < nA;
-        slot_advance<R, GRAD, OPT>(kp, V, bank, park, pend, parked,
-                                    in_prim ? qlist[Q_ADVP * NB + t] : qlist[Q_ADVW * NB + t - nA], in_prim, cnt);
-      } else if ((t -= nA + nW) < nC) {
-        slot_collide<R, GRAD>(kp, V, bank, park, pend, parked, qlist[Q_COLL * NB + t], cnt);
-      } else {
-        t -= nC;
-      }
-      // refill: the threads past the live queues take new histories, one claim per warp
-      const bool want = tid >= nA + nW + nC && t < nE && !exhausted;
+      if (kind == 1 || kind == 2) slot_advance<R, GRAD, OPT>(kp, V, bank, park, pend, parked, slot, kind == 1, cnt);
+      else if (kind == 3) slot_collide<R, GRAD>(kp, V, bank, park, pend, parked, slot, cnt);
+      // refill: new histories, one claim per warp
       const unsigned m = __ballot_sync(kFull, want);
       if (m) {
         const int leader = __ffs(m) - 1;
         unsigned long long g = 0;
-        if (lane == leader) g = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
+        if (lane == leader) g = aborted(kp, polls) ? total : atomicAdd(kp.work_counter, (unsigned long long)__popc(m));
         g = __shfl_sync(kFull, g, leader) + __popc(m & ((1u << lane) - 1u));
         if (want) {
-          if (g < total) slot_start<R, OPT>(kp, V, bank, pend, qlist[Q_EMPTY * NB + t], g, cnt);
+          if (g < total) slot_start<R, GRAD, OPT>(kp, V, bank, pend, rslot, g, cnt);
           else claim_state = 1;
         }
       }
-      __syncthreads();
+      my_slot = kind ? slot : rslot;
+      if ((iter + 1) % every == 0) __syncthreads();   // the next iteration regroups
     }
   }
   // ---- counters ----
@@ -1661,16 +1783,19 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  Particle<R>* pool = reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)warp * kPool;
-  Particle<R>* park = reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)nwarps * kPool + (size_t)warp * kPool;
-  int* pend = reinterpret_cast<int*>(reinterpret_cast<Particle<R>*>(smem + tab) + (size_t)nwarps * kPool * (GRAD ? 2 : 1)) +
-              warp * 2 * kPool;
+  // per warp: its pool of kPool neutrons, parked primaries (gradient runs),
+  // pending event types and parked flags
+  using BankT = Bank<R, GRAD>;
+  const BankT pool(smem + tab + BankT::bytes(kPool) * warp, kPool);
+  const BankT park(smem + tab + BankT::bytes(kPool) * (nwarps + warp), kPool);
+  int* pend = reinterpret_cast<int*>(smem + tab + BankT::bytes(kPool) * nwarps * (GRAD ? 2 : 1)) + warp * 2 * kPool;
   int* parked = pend + kPool;
 
   const unsigned long long total = work_total(kp);
   unsigned cnt[kNumCounters];   // per-thread counts: 32 bits suffice (widened below)
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) cnt[i] = 0;
+  unsigned polls = 0;   // claims made by this thread (abort polling)
 #pragma unroll
   for (int g = 0; g < kPoolGroups; ++g) { pend[g * 32 + lane] = EV_EMPTY; parked[g * 32 + lane] = 0; }
   __syncwarp();
@@ -1685,7 +1810,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
       const int slot = g * 32 + lane;
       const int ty = pend[slot];
       const bool adv = ty == EV_ADV;
-      const bool inprim = adv && pool[slot].vol >= 0;
+      const bool inprim = adv && pool.vol(slot) >= 0;
       m[Q_EMPTY][g] = __ballot_sync(kFull, ty == EV_EMPTY);
       m[Q_ADVP][g] = __ballot_sync(kFull, adv && inprim);
       m[Q_ADVW][g] = __ballot_sync(kFull, adv && !inprim);
@@ -1732,7 +1857,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
       while (taken < n) {
         if (chunk_next >= chunk_end) {
           unsigned long long b = 0;
-          if (lane == 0) b = aborted(kp) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
+          if (lane == 0) b = aborted(kp, polls) ? total : atomicAdd(kp.work_counter, (unsigned long long)kp.chunk);
           b = __shfl_sync(kFull, b, 0);
           if (b >= total) { work_left = false; break; }
           chunk_next = b;
@@ -1740,7 +1865,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
         }
         const int avail = (int)min((unsigned long long)(n - taken), chunk_end - chunk_next);
         if (lane >= taken && lane < taken + avail)
-          slot_start<R, OPT>(kp, V, pool, pend, slot, chunk_next + (lane - taken), cnt);
+          slot_start<R, GRAD, OPT>(kp, V, pool, pend, slot, chunk_next + (lane - taken), cnt);
         chunk_next += avail;
         taken += avail;
       }
@@ -1944,14 +2069,15 @@ cudaError_t occupancy_f64(int variant, bool grad, bool use_grid, int block, size
 }
 
 size_t particle_bytes(int precision) {
-  return precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
+  return precision == TP_FP64 ? sizeof(SecRec<double>) : sizeof(SecRec<float>);
 }
 
 size_t bank_bytes(int variant, int precision, bool grad, int block) {
   variant &= 3;
-  const size_t ps = precision == TP_FP64 ? sizeof(Particle<double>) : sizeof(Particle<float>);
+  const size_t ps = precision == TP_FP64 ? (grad ? Bank<double, true>::kBytes : Bank<double, false>::kBytes)
+                                         : (grad ? Bank<float, true>::kBytes : Bank<float, false>::kBytes);
   if (variant == TP_KERNEL_EVENT)
-    return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQ * block;
+    return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQMax * block;
   if (variant == TP_KERNEL_WARPQ) {
     const size_t slots = (size_t)(block / 32) * kPool;
     return ps * slots * (grad ? 2 : 1) + 2 * sizeof(int) * slots;

@@ -16,6 +16,7 @@ STATUS_NAMES = ["TP_OK", "TP_ERR_INVALID_ARG", "TP_ERR_GEOMETRY", "TP_ERR_CUDA",
                 "TP_ERR_TIMEOUT", "TP_ERR_STATE", "TP_ERR_ABORTED"]
 TP_TEST_SKIP_TABLE_COPY = 1
 TP_TEST_FULL_BUILD = 2
+TP_TEST_SMALL_SEC_QUEUE = 4
 TP_BOX, TP_TUBE, TP_SPHERE = 0, 1, 2
 TP_ROLE_BULK, TP_ROLE_DETECTOR, TP_ROLE_BLACK = 0, 1, 2
 TP_PROC_ABS, TP_PROC_INC, TP_PROC_BRAGG, TP_NPROC = 0, 1, 2, 3
@@ -95,7 +96,7 @@ class tp_run(C.Structure):
                 ("first_history", C.POINTER(C.c_uint64)), ("want_grad", C.c_int),
                 ("stream", C.c_void_p), ("block_size", C.c_int), ("ctas_per_sm", C.c_int),
                 ("records", C.c_void_p), ("n_records", C.c_uint64), ("kernel", C.c_int),
-                ("use_graph", C.c_int), ("secondaries", C.c_int)]
+                ("use_graph", C.c_int), ("secondaries", C.c_int), ("regroup", C.c_int)]
 
 
 class tp_peaks(C.Structure):

@@ -38,21 +38,29 @@ def compare_tallies(m1, e1, m2, e2, frac_3sigma=0.99, max_sigma=5.0, p_min=1e-3)
                 "lonely": int(lonely.sum())}
 
 
-def compare_tallies_unequal(m1, e1, n1, m2, e2, n2, min_count=25.0, **kw):
-    """compare_tallies for samples of very different sizes: a bin whose
-    expected count in the smaller sample (mean x n, unit weights) is below
-    min_count has no usable error estimate there, so such bins are merged
-    into one aggregate bin (sums of means and of variances) before the
-    comparison; the well-populated bins are compared one by one."""
+def compare_tallies_unequal(m1, e1, n1, m2, e2, n2, min_count=100.0, max_sigma=5.5, **kw):
+    """compare_tallies for samples of very different sizes (n1 >> n2).
+
+    Under the hypothesis that both estimate the same means, the per-history
+    variance of a bin is best estimated from the larger sample; the smaller
+    sample's standard error is taken from it (e1 sqrt(n1/n2)) instead of its
+    own count, whose downward fluctuations would shrink its error and inflate
+    the deviation.  A bin whose expected count in the smaller sample (mean x
+    n2, unit weights) is below min_count is far from Gaussian there, so such
+    bins are merged into one aggregate bin before the comparison; the
+    well-populated bins are compared one by one, none beyond max_sigma (5.5:
+    the Poisson tail of a 100-count bin is heavier than the Gaussian one)."""
     m1, e1, m2, e2 = map(lambda a: np.asarray(a, dtype=np.float64), (m1, e1, m2, e2))
-    nmin = float(min(n1, n2))
-    big = 0.5 * (np.abs(m1) + np.abs(m2)) * nmin >= min_count
+    if n1 < n2:
+        return compare_tallies_unequal(m2, e2, n2, m1, e1, n1, min_count, max_sigma, **kw)
+    e2p = e1 * math.sqrt(n1 / n2)
+    big = np.abs(m1) * n2 >= min_count
     rest = ~big
-    agg = lambda a: np.array([a[rest].sum()])
-    aggs = lambda a: np.array([math.sqrt((a[rest] ** 2).sum())])
-    M1 = np.concatenate([m1[big], agg(m1)]); E1 = np.concatenate([e1[big], aggs(e1)])
-    M2 = np.concatenate([m2[big], agg(m2)]); E2 = np.concatenate([e2[big], aggs(e2)])
-    ok, info = compare_tallies(M1, E1, M2, E2, **kw)
+    M1 = np.concatenate([m1[big], [m1[rest].sum()]])
+    E1 = np.concatenate([e1[big], [math.sqrt((e1[rest] ** 2).sum())]])
+    M2 = np.concatenate([m2[big], [m2[rest].sum()]])
+    E2 = np.concatenate([e2p[big], [math.sqrt((e2p[rest] ** 2).sum())]])
+    ok, info = compare_tallies(M1, E1, M2, E2, max_sigma=max_sigma, **kw)
     info["merged_bins"] = int(rest.sum())
     return ok, info
 

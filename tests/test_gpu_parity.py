@@ -168,6 +168,26 @@ def test_launch_shape_does_not_change_results(eng, kernel, block, ctas):
     assert np.allclose(got["sum"], ref["sum"], rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("name", ["slab", "powder", "imaging"])
+@pytest.mark.parametrize("regroup", [2, 3, 4, 7])
+def test_regroup_interval_does_not_change_results(eng, orc, name, regroup):
+    """The event kernel regrouping its bank every few events (each thread
+    running its own neutron in between) gives the sums of regrouping every
+    event, history for history (FP64), and the oracle's."""
+    n = 20_011
+    desc = {"slab": lambda: W.slab(g=3.0, n_histories=n, precision="f64"),
+            "powder": lambda: W.powder(n_histories=n, precision="f64"),
+            "imaging": lambda: W.imaging(n_histories=n, precision="f64", psd_bins=32)}[name]()
+    ref = gpu_run(eng, desc, n, kernel=2, regroup=1)["raw"]
+    got = gpu_run(eng, desc, n, kernel=2, regroup=regroup)
+    assert got["scene"].launch()[0] == 2
+    assert np.allclose(got["raw"]["sum"], ref["sum"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(got["raw"]["sumsq"], ref["sumsq"], rtol=1e-12, atol=1e-15)
+    if name == "slab":
+        o = orc.OracleScene(desc).run(n)
+        assert np.allclose(got["raw"]["sum"], o["sum"], rtol=1e-9, atol=1e-12)
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_64_register_build_matches_the_80_register_build(eng, orc, kernel):
     """Asking for 4 blocks of 256 per SM selects the 64-register build of a
@@ -472,19 +492,22 @@ def test_batched_fp32_tallies_and_gradients_statistically_match(eng, orc, kernel
 
 
 def test_queued_secondaries_over_several_chunks_fp64_match_oracle(eng, orc):
-    """A run longer than one chunk of the secondary queue (2^25 records hold
-    the secondaries of 2^22 histories): chunk after chunk of histories, each
-    followed by the second pass, sums to the oracle's tallies and gradient
-    tallies history for history."""
-    counts = np.array([2_600_000, 2_400_000], dtype=np.int64)
+    """A run longer than one chunk of the secondary queue (shrunk by a test
+    flag to 2^20 records, the secondaries of 2^20 / 6 histories): chunk after
+    chunk of histories, each followed by the second pass, sums to the
+    oracle's tallies and gradient tallies history for history."""
+    from paper_2304_06226_gb300 import native as N
+    counts = np.array([520_000, 480_000], dtype=np.int64)
     desc = W.batched(n_instances=2, precision="f64")
     desc["instances"]["counts"] = counts
     sc = eng.Scene(desc)
+    sc.set_test_flags(N.TP_TEST_SMALL_SEC_QUEUE)
     sc.run(want_grad=True, kernel=2, secondaries=2)
     torch.cuda.synchronize()
     c = sc.counters()
     assert c["histories"] == counts.sum() and c["secondaries"] > counts.sum()
-    assert sc.launch_count() == 4   # two chunks, two passes each
+    chunk = (1 << 20) // 6
+    assert sc.launch_count() == 2 * -(-int(counts.sum()) // chunk)   # two passes per chunk
     osc = orc.OracleScene(desc)
     for q in range(2):
         o = osc.run(int(counts[q]), inst=q, want_grad=True)
