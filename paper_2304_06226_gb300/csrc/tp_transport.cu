@@ -61,6 +61,14 @@ template <> struct Tr<float> {
   }
   static __device__ __forceinline__ float nudge(float m) { return 1e-5f * fmaxf(1.0f, m); }
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+  // -ln(u01(a)), the step of Eq. eStepLength2 per unit of Sigma_g: the
+  // hardware logarithm (absolute error below 4e-7 on [0.5, 1)), except within
+  // 1e-6 of 1 where that error could reach the value itself and log1p of the
+  // exact u - 1 is taken
+  static __device__ __forceinline__ float neg_log_u01(uint32_t a) {
+    const float u = u01(a);
+    return (a >> 8) < 0xFFFFF0u ? -__logf(u) : -log1pf(u - 1.0f);
+  }
   static constexpr float kPi = 3.14159265358979323846f;
   static constexpr float kTwoPi = 6.283185307179586f;
   static constexpr float kFourPi = 12.566370614359172f;
@@ -70,6 +78,7 @@ template <> struct Tr<double> {
     return ((double)a + 0.5) * 2.3283064365386963e-10;  // (a + 1/2) 2^-32
   }
   static __device__ __forceinline__ double nudge(double m) { return 1e-9 * fmax(1.0, m); }
+  static __device__ __forceinline__ double neg_log_u01(uint32_t a) { return -log(u01(a)); }
   static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
   static constexpr double kPi = 3.14159265358979323846;
   static constexpr double kTwoPi = 6.283185307179586;
@@ -960,7 +969,7 @@ __device__ int advance(const KParams<R>& kp, const View<R>& V, Particle<R>& P, c
   R l = INF;
   if (sig_g > R(0)) {
     a.r0 = philox(make_uint4(P.k, P.sub0, P.hid, P.inst), kp.key0, kp.key1);
-    l = -d_log(Tr<R>::u01(a.r0.x)) / sig_g;
+    l = Tr<R>::neg_log_u01(a.r0.x) / sig_g;
   }
   // next boundary
   R db;
@@ -1447,6 +1456,12 @@ __device__ __forceinline__ void q_push(unsigned short* list, int* count, bool pr
 
 template <typename R>
 __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst, R (&ip)[kMaxPar], R* dR) {
+  if (kp.npar == 0) {   // no instance parameters: nothing to read
+#pragma unroll
+    for (int i = 0; i < kMaxPar; ++i) ip[i] = R(0);
+    *dR = R(0);
+    return;
+  }
   const R* q = kp.inst_params + (size_t)inst * kMaxPar;
 #pragma unroll
   for (int i = 0; i < kMaxPar; ++i) ip[i] = __ldg(q + i);
