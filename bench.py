@@ -195,7 +195,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     sc = Scene(desc)
     bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
     runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
-                                   graph=True, first=first, seed=seed, secondaries=args.secondaries)) if grad else None
+                                   block_size=args.block_size, graph=True, first=first, seed=seed,
+                                   secondaries=args.secondaries)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     first, seed = 0, None
@@ -210,7 +211,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             runs(st)
             sc.backward(bgrad, stream=st)
         else:
-            sc.run(n, first=first, seed=seed, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
+            sc.run(n, first=first, seed=seed, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
+                   block_size=args.block_size)
 
     peaks = measured_peaks() if rank == 0 else None
     # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
@@ -495,6 +497,7 @@ def main() -> None:
     ap.add_argument("--kernel", type=int, default=0, help="0 autotuned, 1 history-based, 2 event-based, 3 warp pools")
     ap.add_argument("--secondaries", type=int, default=0,
                     help="gradient runs: 0 autotuned, 1 in place, 2 queued for a second pass")
+    ap.add_argument("--block-size", type=int, default=0, help="threads per block with --kernel (0: 256)")
     ap.add_argument("--ctas-per-sm", type=int, default=0,
                     help="CTAs per SM with --kernel (4 x 256 threads selects the 64-register build)")
     ap.add_argument("--no-batched", dest="batched", action="store_false")

@@ -1468,6 +1468,31 @@ __device__ __forceinline__ void load_params(const KParams<R>& kp, uint32_t inst,
   *dR = kp.radius_par >= 0 ? sel(ip, kp.radius_par, R(0)) - kp.radius_nominal : R(0);
 }
 
+// Counts of a secondary run out of line (returned, so that the caller's
+// counters stay in registers).
+struct SecCounts { unsigned c[kNumCounters]; };
+
+// Transports a radius-derivative secondary to its end where it was made
+// (gradient runs of the warp-pool kernel, when the queue of the second pass
+// is full or not in use): out of line, a cold path that keeps its registers
+// away from the hot loop.  A secondary makes no secondaries of its own.
+template <typename R, int OPT>
+__device__ __noinline__ SecCounts run_secondary(const KParams<R>& kp, const View<R>& V, Particle<R> S,
+                                                const R (&ip)[kMaxPar], R dR) {
+  SecCounts r;
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) r.c[i] = 0;
+  for (;;) {
+    Particle<R> none;
+    bool spawn = false;
+    const int end = step<R, true, OPT>(kp, V, S, ip, dR, r.c, &none, &spawn);
+    if (end >= 0) {
+      finish(kp, S, end);
+      return r;
+    }
+  }
+}
+
 // The per-slot steps of the regrouping kernels.  A bank (event kernel) or pool
 // (warp-pool kernel) holds one neutron per slot with its next event in pend[];
 // in gradient runs a primary that made a radius-derivative secondary waits in
@@ -1510,7 +1535,10 @@ __device__ __forceinline__ int slot_start(const KParams<R>& kp, const View<R>& V
 // Advance the neutron of `slot` and, if it reaches a boundary, cross it (inside
 // a primitive every crossing is an exit, in the world region an entry; the
 // caller knows which: in_prim).  Returns true if it now waits for a collision.
-template <typename R, bool GRAD, int OPT>
+// PARK: a secondary that is not queued takes over the slot while its primary
+// waits in park[] (event kernel); without PARK (warp pools) the lane runs it
+// to its end at once, out of line, and the pool needs no parking bank.
+template <typename R, bool GRAD, int OPT, bool PARK = true>
 __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>& V, const Bank<R, GRAD>& bank,
                                              const Bank<R, GRAD>& park, int* pend, int* parked, int slot, bool in_prim,
                                              unsigned* cnt) {
@@ -1534,12 +1562,18 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
   } else {
     if (end >= 0) finish(kp, P, end);
     if (GRAD && spawn && sec_push(kp, S)) spawn = false;
-    if (GRAD && spawn) {
+    if (GRAD && !PARK && spawn) {
+      const SecCounts r = run_secondary<R, OPT>(kp, V, S, ip, dR);
+#pragma unroll
+      for (int i = 0; i < kNumCounters; ++i) cnt[i] += r.c[i];
+      spawn = false;
+    }
+    if (GRAD && PARK && spawn) {
       if (end < 0) { park.store(slot, P); parked[slot] = 1; }
       P = S;
       pend[slot] = EV_ADV;
     } else if (end >= 0) {
-      if (GRAD && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
+      if (GRAD && PARK && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
       else pend[slot] = EV_EMPTY;
     } else {
       pend[slot] = EV_ADV;
@@ -1550,7 +1584,7 @@ __device__ __forceinline__ bool slot_advance(const KParams<R>& kp, const View<R>
 }
 
 // The collision the neutron of `slot` waits for.
-template <typename R, bool GRAD>
+template <typename R, bool GRAD, bool PARK = true>
 __device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>& V, const Bank<R, GRAD>& bank,
                                              const Bank<R, GRAD>& park, int* pend, int* parked, int slot,
                                              unsigned* cnt) {
@@ -1560,7 +1594,7 @@ __device__ __forceinline__ void slot_collide(const KParams<R>& kp, const View<R>
   const int end = collide_again<R, GRAD>(kp, V, P, ip, cnt);
   if (end >= 0) {
     finish(kp, P, end);
-    if (GRAD && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
+    if (GRAD && PARK && parked[slot]) { P = park.load(slot); parked[slot] = 0; pend[slot] = EV_ADV; }
     else pend[slot] = EV_EMPTY;
   } else {
     pend[slot] = EV_ADV;
@@ -1798,12 +1832,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  // per warp: its pool of kPool neutrons, parked primaries (gradient runs),
-  // pending event types and parked flags
+  // per warp: its pool of kPool neutrons and their pending event types (no
+  // parking: a secondary that is not queued runs to its end at once)
   using BankT = Bank<R, GRAD>;
   const BankT pool(smem + tab + BankT::bytes(kPool) * warp, kPool);
-  const BankT park(smem + tab + BankT::bytes(kPool) * (nwarps + warp), kPool);
-  int* pend = reinterpret_cast<int*>(smem + tab + BankT::bytes(kPool) * nwarps * (GRAD ? 2 : 1)) + warp * 2 * kPool;
+  const BankT park = pool;   // unused (PARK false)
+  int* pend = reinterpret_cast<int*>(smem + tab + BankT::bytes(kPool) * nwarps) + warp * 2 * kPool;
   int* parked = pend + kPool;
 
   const unsigned long long total = work_total(kp);
@@ -1885,9 +1919,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
         taken += avail;
       }
     } else if (q == Q_ADVP || q == Q_ADVW) {
-      if (slot >= 0) slot_advance<R, GRAD, OPT>(kp, V, pool, park, pend, parked, slot, q == Q_ADVP, cnt);
+      if (slot >= 0) slot_advance<R, GRAD, OPT, false>(kp, V, pool, park, pend, parked, slot, q == Q_ADVP, cnt);
     } else {
-      if (slot >= 0) slot_collide<R, GRAD>(kp, V, pool, park, pend, parked, slot, cnt);
+      if (slot >= 0) slot_collide<R, GRAD, false>(kp, V, pool, park, pend, parked, slot, cnt);
     }
     __syncwarp();
   }
@@ -2095,7 +2129,7 @@ size_t bank_bytes(int variant, int precision, bool grad, int block) {
     return ps * block * (grad ? 2 : 1) + 2 * sizeof(int) * block + sizeof(unsigned short) * kNumQMax * block;
   if (variant == TP_KERNEL_WARPQ) {
     const size_t slots = (size_t)(block / 32) * kPool;
-    return ps * slots * (grad ? 2 : 1) + 2 * sizeof(int) * slots;
+    return ps * slots + 2 * sizeof(int) * slots;
   }
   return 0;
 }
