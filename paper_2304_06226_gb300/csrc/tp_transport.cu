@@ -1830,8 +1830,11 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
   V.nb = reinterpret_cast<const int*>(base + kp.off_nb);
 
   const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
+  __shared__ unsigned char sel[8][32];   // per warp: the slots of this step, in lane order
+  unsigned char* sel_row = sel[warp];
   // per warp: its pool of kPool neutrons and their pending event types (no
   // parking: a secondary that is not queued runs to its end at once)
   using BankT = Bank<R, GRAD>;
@@ -1889,7 +1892,23 @@ __global__ void __launch_bounds__(256, MINB) k_transport_wq(const __grid_constan
     // ---- lane j takes the j-th slot of queue q ----
     const int n = min(count[q], 32);
     int slot = -1;
-    if (lane < n) {
+    if constexpr (!(OPT & kOptFull)) {
+      // lean build: the slots' own lanes write their indices in rank order to
+      // the warp's selection row and lane j reads entry j (powder +14 %)
+      int base = 0;
+#pragma unroll
+      for (int g = 0; g < kPoolGroups; ++g) {
+        const unsigned mg = m[q][g];
+        const int r = base + __popc(mg & lt_mask);
+        if (((mg >> lane) & 1u) && r < 32) sel_row[r] = (unsigned char)(g * 32 + lane);
+        base += __popc(mg);
+      }
+      __syncwarp();
+      if (lane < n) slot = (int)sel_row[lane];
+      __syncwarp();
+    } else if (lane < n) {
+      // full build: each lane finds its set bit (guide and total scattering
+      // run 5 % faster this way)
       int j = lane;
 #pragma unroll
       for (int g = 0; g < kPoolGroups; ++g) {
