@@ -30,12 +30,11 @@ sys.path.insert(0, str(ROOT))
 METRIC = "histories/s on 1 GB300: plain vs batched+adjoint, at matched tally error"
 UNIT = "histories/s"
 POWDER_N = 100_000_000
-# Thread instructions the history-based kernel (one neutron per thread, no
-# regrouping overhead) executed per history, from ncu
-# smsp__thread_inst_executed.sum / histories on a small case of each workload:
-# an implementation's count, reported beside the algorithmic one below.
-EXECUTED_INST_PER_HISTORY = {"powder": 4264, "guide": 2273, "imaging": 3996, "slab": 5902, "batched": 13076,
-                             "chopper": 1766, "total_scattering": 3385}
+# Thread instructions per history the kernel of the workload's benchmark line
+# executes (ncu smsp__inst_executed.sum x active lanes / histories on a small
+# case of the same launch): an implementation's count, reported beside the
+# algorithmic one below.  Measured for the powder workload's warp-pool kernel.
+EXECUTED_INST_PER_HISTORY = {"powder": 5080}
 # Algorithmic lane operations of the method per step type, counted from its
 # formulas (not from any kernel):
 #   every event (biased flight, Eq. eStepLength2, and weight, Eq. eWeight):
@@ -61,11 +60,12 @@ def algorithmic_ops_per_history(counters: dict) -> float:
 
 # DRAM bytes of one full-size step of the kernel variant the autotuner picks
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload,
-# variant): powder, one launch of the 64-register warp-pool kernel; batched,
-# the two passes of a queued-secondaries run (measured on 4e7 histories of the
-# same instance mix and scaled by histories: the queue traffic grows with them).
-TRAFFIC_PER_LAUNCH = {("powder", 3): 769792 + 31387904,
-                      ("batched", 2): int((174452480 + 11512364032 + 11701826048 + 134533376) * 591711879 / 4e7)}
+# variant): powder, the warp-pool launch (measured on 1e7 histories: the
+# tables' and tallies' cold misses, which do not grow with the histories);
+# batched, the two passes of a queued-secondaries step (measured on 4e6
+# histories of the same instance mix and scaled by histories: the queue grows
+# with them).
+TRAFFIC_PER_LAUNCH = {("powder", 3): 143104, ("batched", 2): 237353386023}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
@@ -317,7 +317,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                      "peak_basis": (f"measured FP32 FMA lane rate of this GPU (tp_measure_peaks, "
                                     f"{peaks['sm_clock_mhz']:.0f} MHz during the measurement)"),
                      "executed": ({"per_unit": exec_ph, "frac": exec_ph * tot / t_s / peak,
-                                   "basis": "thread instructions per history of the history-based kernel (ncu)"}
+                                   "basis": "thread instructions per history this workload's kernel executes (ncu, "
+                                            "small case of the same launch)"}
                                   if exec_ph else None)},
         "peaks": peaks,
         "kernel_ms": kernel_ms,
