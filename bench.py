@@ -196,7 +196,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     bgrad = torch.ones(sc.n_inst, sc.total_bins, dtype=torch.float64, device="cuda") if grad else None
     runs = (lambda st=None: sc.run(want_grad=True, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
                                    block_size=args.block_size, graph=True, first=first, seed=seed,
-                                   secondaries=args.secondaries)) if grad else None
+                                   secondaries=args.secondaries, stage=args.stage)) if grad else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     first, seed = 0, None
@@ -212,7 +212,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             sc.backward(bgrad, stream=st)
         else:
             sc.run(n, first=first, seed=seed, stream=st, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
-                   block_size=args.block_size)
+                   block_size=args.block_size, stage=args.stage)
 
     peaks = measured_peaks() if rank == 0 else None
     # ---- warm-up (the library is ahead-of-time compiled; the first run autotunes) ----
@@ -276,7 +276,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             g = sc.backward(bgrad)
             host_grad[:, : sc.n_par] = g.cpu().numpy()
         else:
-            sc.run(n, first=first, seed=seed, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm)
+            sc.run(n, first=first, seed=seed, kernel=args.kernel, ctas_per_sm=args.ctas_per_sm,
+                   block_size=args.block_size, stage=args.stage)
         for t in range(len(sc.tally_bins)):
             o = sc.tally_off[t]
             NN.tp_read_tallies(sc.handle, t, q, host_mean[o:].ctypes.data, host_err[o:].ctypes.data, False)
@@ -306,7 +307,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "data": "synthetic",
         "config": workload_config(args.workload, label, {
             "histories_per_step_per_gpu": n, "tallies": "FP64 sum w, sum w^2 per bin",
-            "launch": dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch())),
+            "launch": sc.launch_info(),
             "parallelism": f"history ids sharded over {world} GPU(s), one FP64 all-reduce of the tallies"}),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "lane-ops/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -378,7 +379,7 @@ def run_batched(args, W, Scene, torch, peaks) -> dict:
     m = raw["sum"].sum() / N
     rel = math.sqrt(max(raw["sumsq"].sum() / N - m * m, 0.0) / (N - 1)) / m
     hist_s = total * steps / t
-    launch = dict(zip(("kernel", "block", "ctas_per_sm"), sc.launch()))
+    launch = sc.launch_info()
     launches_per_step = sc.launch_count() + 1   # transport passes + backward
     fw_s = sum(fw_ms) / 1e3
     alg_ph = algorithmic_ops_per_history(sc.counters())
@@ -499,6 +500,8 @@ def main() -> None:
     ap.add_argument("--secondaries", type=int, default=0,
                     help="gradient runs: 0 autotuned, 1 in place, 2 queued for a second pass")
     ap.add_argument("--block-size", type=int, default=0, help="threads per block with --kernel (0: 256)")
+    ap.add_argument("--stage", type=int, default=0,
+                    help="with --kernel: scene tables 0 staged when they fit, 1 staged, 2 read from device memory")
     ap.add_argument("--ctas-per-sm", type=int, default=0,
                     help="CTAs per SM with --kernel (4 x 256 threads selects the 64-register build)")
     ap.add_argument("--no-batched", dest="batched", action="store_false")

@@ -264,10 +264,17 @@ typedef struct {
  *   chosen by the autotuner with kernel 0, else 1.  Results do not depend on
  *   the choice (each secondary has its own random numbers).
  * regroup (event kernel, plain runs): the bank is regrouped every `regroup`
- *   events -- sorted into sub-queues by event type, primitive shape and
- *   material, so that a warp runs one kind of event -- and in between each
- *   thread runs the next events of the neutron it holds; 0 = chosen by the
- *   autotuner with kernel 0 (1 or 4), else 1.  Results do not depend on it. */
+ *   events -- sorted into queues by event type (advance inside a primitive,
+ *   advance in the world region, collision, refill), so that a warp runs one
+ *   kind of event -- and in between each thread runs the next events of the
+ *   neutron it holds; 0 = chosen by the autotuner with kernel 0 (1 or 4),
+ *   else 1.  Results do not depend on it.
+ * stage (explicit kernel): where the kernel reads the scene tables from: 0 =
+ *   copied into shared memory when they fit (at most 96 KiB beside the
+ *   neutron bank), 1 = copied into shared memory (TP_ERR_INVALID_ARG if they
+ *   do not fit), 2 = read from device memory through L1/L2 (leaves room for
+ *   more blocks per SM).  With kernel 0 the autotuner decides and stage must
+ *   be 0.  Results do not depend on it. */
 typedef struct {
   uint64_t seed;
   const uint64_t* n_histories;
@@ -282,6 +289,7 @@ typedef struct {
   int use_graph;
   int secondaries;
   int regroup;
+  int stage;
 } tp_run;
 
 enum { TP_KERNEL_AUTO = 0, TP_KERNEL_HISTORY = 1, TP_KERNEL_EVENT = 2, TP_KERNEL_WARPQ = 3 };
@@ -376,6 +384,22 @@ tp_status tp_get_launch(tp_scene* s, int* kernel, int* block_size, int* ctas_per
  * any run or if the run had no histories.  No device work. */
 int tp_get_launch_count(const tp_scene* s);
 
+/* The complete launch configuration of the scene's last tp_run_histories
+ * (after the autotuner, if it ran): transport kernel (TP_KERNEL_*), threads
+ * per block, CTAs per SM, tables staged in shared memory (1) or read from
+ * device memory (0), register build (80 or 64 registers per thread: the
+ * kernels are compiled for 3 and for 4 blocks of 256 threads per SM), full
+ * build (1: mirrors, choppers, per-order scorers, moderator guns and
+ * separate absorption factors compiled in; 0: the lean build for scenes
+ * without them), regrouping interval of the event kernel, secondaries queued
+ * for a second pass (1) or transported in place (0), and transport kernels
+ * launched.  All zero before the first run.  Errors: TP_ERR_INVALID_ARG for
+ * NULL arguments. */
+typedef struct {
+  int kernel, block_size, ctas_per_sm, staged, registers, full_build, regroup, queued_secondaries, launches;
+} tp_launch_info;
+tp_status tp_get_launch_info(const tp_scene* s, tp_launch_info* out);
+
 /* Total bins over all tallies (per instance). */
 int tp_total_bins(const tp_scene* s);
 
@@ -396,7 +420,7 @@ int tp_total_bins(const tp_scene* s);
  *    read as in tp_create_scene, tp_set_materials, tp_set_bias and
  *    tp_run_histories, with these restrictions (TP_ERR_INVALID_ARG
  *    otherwise): r->want_grad, r->records, r->use_graph and r->secondaries
- *    must be 0/NULL, r->regroup 0 or 1, and r->kernel 0 or TP_KERNEL_HISTORY: the call always
+ *    must be 0/NULL, r->regroup 0 or 1, r->stage 0 or 1, and r->kernel 0 or TP_KERNEL_HISTORY: the call always
  *    runs the history-based kernel with the tables staged when they fit, and
  *    builds no uniform grid, so a scene of many primitives tests all of them
  *    at every step of the world region (same results, more work).

@@ -163,6 +163,7 @@ struct tp_scene {
   bool stage_pending = false;
   // launch configuration: last used, and the autotuned choice per gradient mode
   int kernel = 0, block = 0, ctas_per_sm = 0;
+  LaunchCfg last_cfg{};   // the last run's complete configuration
   int launches = 0;   // transport kernels of the last run
   int smem_optin = 0; // shared memory a block may use on this device (queried once)
   int tuned_kernel[2] = {0, 0}, tuned_block[2] = {0, 0}, tuned_stage[2] = {-1, -1}, tuned_hi[2] = {-1, -1};
@@ -1228,6 +1229,9 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   s->h_stage[s->n_inst] = total;
   if (total == 0) return TP_OK;
   if (r->secondaries < 0 || r->secondaries > 2) return fail(TP_ERR_INVALID_ARG, "secondaries %d", r->secondaries);
+  if (r->stage < 0 || r->stage > 2) return fail(TP_ERR_INVALID_ARG, "stage %d: need 0, 1 or 2", r->stage);
+  if (r->stage != 0 && r->kernel == TP_KERNEL_AUTO)
+    return fail(TP_ERR_INVALID_ARG, "stage %d needs an explicit kernel (the autotuner picks the staging)", r->stage);
   const bool tune = r->kernel == TP_KERNEL_AUTO && s->tuned_kernel[grad] == 0;
   if (grad && (r->secondaries == 2 || (r->secondaries == 0 && (tune || (r->kernel == TP_KERNEL_AUTO && s->tuned_defer))))) {
     tp_status e = ensure_sec(s, total);   // before any capture: it may allocate
@@ -1252,8 +1256,8 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
     if (block == 0) block = s->tuned_block[grad];
   }
   LaunchCfg cfg;
-  tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg,
-                        r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : -1,
+  const int stage = r->kernel == TP_KERNEL_AUTO ? s->tuned_stage[grad] : (r->stage == 0 ? -1 : (r->stage == 1 ? 1 : 0));
+  tp_status e = resolve(s, grad, kernel, block, r->ctas_per_sm, &cfg, stage,
                         r->kernel == TP_KERNEL_AUTO && r->ctas_per_sm == 0 ? s->tuned_hi[grad] : -1);
   if (e != TP_OK) return e;
   if (grad) cfg.defer = r->secondaries == 2 || (r->secondaries == 0 && r->kernel == TP_KERNEL_AUTO && s->tuned_defer);
@@ -1275,6 +1279,7 @@ tp_status tp_run_histories(tp_scene* s, const tp_run* r) {
   s->kernel = cfg.kernel;
   s->block = cfg.block;
   s->ctas_per_sm = cfg.ctas;
+  s->last_cfg = cfg;
   if (grad && cfg.defer) {
     const unsigned long long chunk = std::max(1ull, s->sec_cap / kSecPerHistory);
     s->launches = (int)(2 * ((total + chunk - 1) / chunk));
@@ -1418,6 +1423,23 @@ tp_status tp_set_test_flags(tp_scene* s, int flags) {
 
 int tp_get_launch_count(const tp_scene* s) { return s ? s->launches : 0; }
 
+tp_status tp_get_launch_info(const tp_scene* s, tp_launch_info* out) {
+  if (!s || !out) return fail(TP_ERR_INVALID_ARG, "null argument");
+  *out = tp_launch_info{};
+  if (s->kernel == 0) return TP_OK;
+  const LaunchCfg& c = s->last_cfg;
+  out->kernel = c.kernel;
+  out->block_size = c.block;
+  out->ctas_per_sm = c.ctas;
+  out->staged = c.stage ? 1 : 0;
+  out->registers = c.hi ? 64 : 80;
+  out->full_build = c.full ? 1 : 0;
+  out->regroup = c.regroup;
+  out->queued_secondaries = c.defer ? 1 : 0;
+  out->launches = s->launches;
+  return TP_OK;
+}
+
 tp_status tp_get_launch(tp_scene* s, int* kernel, int* block, int* ctas) {
   if (!s || !kernel || !block || !ctas) return fail(TP_ERR_INVALID_ARG, "null argument");
   *kernel = s->kernel;
@@ -1498,8 +1520,8 @@ extern "C" tp_status tp_run_histories_noalloc(const tp_scene_desc* d, const tp_m
   if (r->want_grad || r->records) return fail(TP_ERR_INVALID_ARG, "no gradients or records in the allocation-free call");
   if (r->kernel != TP_KERNEL_AUTO && r->kernel != TP_KERNEL_HISTORY)
     return fail(TP_ERR_INVALID_ARG, "kernel %d: the allocation-free call runs the history kernel only", r->kernel);
-  if (r->use_graph || r->secondaries || r->regroup > 1)
-    return fail(TP_ERR_INVALID_ARG, "the allocation-free call takes no graph, secondaries or regroup option");
+  if (r->use_graph || r->secondaries || r->regroup > 1 || r->stage == 2)
+    return fail(TP_ERR_INVALID_ARG, "the allocation-free call takes no graph, secondaries, regroup or unstaged-table option");
   if (d->n_instances < 1 || d->n_instances > TP_NOALLOC_MAX_INSTANCES)
     return fail(TP_ERR_INVALID_ARG, "n_instances %d: the allocation-free call takes 1..%d", d->n_instances,
                 TP_NOALLOC_MAX_INSTANCES);

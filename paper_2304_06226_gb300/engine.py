@@ -153,12 +153,15 @@ class Scene:
 
     def run(self, n=None, seed: int | None = None, first=None, want_grad: bool = False, stream=None,
             block_size: int = 0, ctas_per_sm: int = 0, records: torch.Tensor | None = None,
-            kernel: int = 0, graph: bool = False, secondaries: int = 0, regroup: int = 0) -> None:
+            kernel: int = 0, graph: bool = False, secondaries: int = 0, regroup: int = 0,
+            stage: int = 0) -> None:
         """Queue histories on `stream` (default: torch's current stream).  n: per
         instance counts (int for one instance, array for many; default: the
         workload's counts).  secondaries: 0 autotuned, 1 in place, 2 queued for a
         second pass (gradient runs).  regroup: events between regroupings of
-        the event kernel (0 = autotuned or 1)."""
+        the event kernel (0 = autotuned or 1).  stage (explicit kernel): scene
+        tables 0 = in shared memory when they fit, 1 = in shared memory, 2 =
+        read from device memory."""
         counts = self.counts if n is None else np.broadcast_to(np.asarray(n, dtype=np.uint64),
                                                                (self.n_inst,))
         cnt = np.ascontiguousarray(counts, dtype=np.uint64)
@@ -171,7 +174,7 @@ class Scene:
                      int(want_grad), _stream_handle(stream), block_size, ctas_per_sm,
                      None if records is None else records.data_ptr(),
                      0 if records is None else records.numel() * records.element_size() // C.sizeof(N.tp_record),
-                     kernel, int(graph), int(secondaries), int(regroup))
+                     kernel, int(graph), int(secondaries), int(regroup), int(stage))
         N.tp_run_histories(self.handle, r)
 
     def tally(self, t: int, instance: int = 0, device: bool = True):
@@ -243,6 +246,10 @@ class Scene:
     def launch(self) -> tuple[int, int, int]:
         """(kernel, block size, CTAs per SM) of the last run."""
         return N.tp_get_launch(self.handle)
+
+    def launch_info(self) -> dict:
+        """The last run's complete launch configuration (tp_get_launch_info)."""
+        return N.tp_get_launch_info(self.handle)
 
     def launch_count(self) -> int:
         """Transport kernels the last run launched (two per chunk with queued secondaries)."""

@@ -96,7 +96,13 @@ class tp_run(C.Structure):
                 ("first_history", C.POINTER(C.c_uint64)), ("want_grad", C.c_int),
                 ("stream", C.c_void_p), ("block_size", C.c_int), ("ctas_per_sm", C.c_int),
                 ("records", C.c_void_p), ("n_records", C.c_uint64), ("kernel", C.c_int),
-                ("use_graph", C.c_int), ("secondaries", C.c_int), ("regroup", C.c_int)]
+                ("use_graph", C.c_int), ("secondaries", C.c_int), ("regroup", C.c_int),
+                ("stage", C.c_int)]
+
+
+class tp_launch_info(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("kernel", "block_size", "ctas_per_sm", "staged", "registers", "full_build",
+                                      "regroup", "queued_secondaries", "launches")]
 
 
 class tp_peaks(C.Structure):
@@ -126,6 +132,7 @@ SIGNATURES = {
     "tp_get_launch": (C.c_int, [SCENE_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tp_total_bins": (C.c_int, [SCENE_P]),
     "tp_get_launch_count": (C.c_int, [SCENE_P]),
+    "tp_get_launch_info": (C.c_int, [SCENE_P, C.POINTER(tp_launch_info)]),
     "tp_abort": (C.c_int, [SCENE_P]),
     "tp_measure_peaks": (C.c_int, [C.POINTER(tp_peaks), C.c_void_p]),
     "tp_set_test_flags": (C.c_int, [SCENE_P, C.c_int]),
@@ -250,6 +257,12 @@ def tp_get_launch(scene: int) -> tuple[int, int, int]:
     k, b, c = C.c_int(), C.c_int(), C.c_int()
     check(lib.tp_get_launch(scene, C.byref(k), C.byref(b), C.byref(c)), "tp_get_launch")
     return k.value, b.value, c.value
+
+
+def tp_get_launch_info(scene: int) -> dict:
+    out = tp_launch_info()
+    check(lib.tp_get_launch_info(scene, C.byref(out)), "tp_get_launch_info")
+    return {n: getattr(out, n) for n, _ in tp_launch_info._fields_}
 
 
 def tp_get_launch_count(scene: int) -> int:

@@ -38,7 +38,7 @@ def marshal(engine, desc):
     return d, mats, len(desc["materials"]), bias, keep + mkeep + [bias]
 
 
-def call_noalloc(engine, N, desc, n, seed, counters=True, kernel=0):
+def call_noalloc(engine, N, desc, n, seed, counters=True, kernel=0, stage=0):
     """One call; returns (status, sums, squares, counters or None)."""
     d, mats, nm, bias, keep = marshal(engine, desc)
     tb = sum(t["bins"][0] * t["bins"][1] for t in desc["tallies"])
@@ -46,7 +46,7 @@ def call_noalloc(engine, N, desc, n, seed, counters=True, kernel=0):
     out_sq = torch.zeros(tb, dtype=torch.float64, device="cuda")
     counts = np.array([n], dtype=np.uint64)
     run = N.tp_run(seed, counts.ctypes.data_as(C.POINTER(C.c_uint64)), None, 0,
-                   torch.cuda.current_stream().cuda_stream, 0, 0, None, 0, kernel, 0)
+                   torch.cuda.current_stream().cuda_stream, 0, 0, None, 0, kernel, 0, 0, 0, stage)
     cnt = (C.c_int64 * 8)() if counters else None
     st = N.lib.tp_run_histories_noalloc(C.byref(d), mats, nm, bias.ctypes.data_as(N.DP) if bias.size else None,
                                         C.byref(run), out_sum.data_ptr(), out_sq.data_ptr(), cnt)
@@ -115,6 +115,8 @@ def test_noalloc_rejects_other_kernels_and_large_tables(env):
     desc = W.powder(n_histories=1000)
     st, *_ = call_noalloc(engine, N, desc, 1000, seed=1, kernel=N.TP_KERNEL_EVENT)
     assert st == N.TP_ERR_INVALID_ARG and "history kernel" in N.tp_last_error()
+    st, *_ = call_noalloc(engine, N, desc, 1000, seed=1, stage=2)   # tables read from device memory
+    assert st == N.TP_ERR_INVALID_ARG and "unstaged" in N.tp_last_error()
     big = W.imaging(n_histories=1000)      # 1000 primitives: tables above 64 KiB
     st, *_ = call_noalloc(engine, N, big, 1000, seed=1)
     assert st == N.TP_ERR_INVALID_ARG, N.tp_last_error()
