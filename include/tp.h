@@ -167,7 +167,9 @@ typedef struct {
 /* Scene description.  The world is a vacuum box (params = half extents) or
  * sphere (params = (0, radius, 0)) containing every primitive; leaving it ends
  * a history (EXIT of volume -1).  Primitives must not overlap (touching is
- * allowed).  inst_params is [n_instances][n_params]; param_kind[n_params]. */
+ * allowed); at most TP_MAX_PRIMS of them.  inst_params is
+ * [n_instances][n_params]; param_kind[n_params]. */
+#define TP_MAX_PRIMS 16777214
 typedef struct {
   int world_shape;
   double world_centre[3], world_params[3];

@@ -938,6 +938,7 @@ static tp_status describe(const tp_scene_desc* d, tp_scene* s) {
     return fail(TP_ERR_INVALID_ARG, "world half extents must be positive");
   if (d->world_shape == TP_SPHERE && !(d->world_params[1] > 0)) return fail(TP_ERR_INVALID_ARG, "world radius must be positive");
   if (d->n_prims < 0 || (d->n_prims > 0 && !d->prims)) return fail(TP_ERR_INVALID_ARG, "prims");
+  if (d->n_prims > TP_MAX_PRIMS) return fail(TP_ERR_INVALID_ARG, "%d primitives: at most %d", d->n_prims, TP_MAX_PRIMS);
   if (d->n_mirrors < 0 || (d->n_mirrors > 0 && !d->mirrors)) return fail(TP_ERR_INVALID_ARG, "mirrors");
   if (d->n_choppers < 0 || (d->n_choppers > 0 && !d->choppers)) return fail(TP_ERR_INVALID_ARG, "choppers");
   if (d->n_tallies < 0 || d->n_tallies > TP_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))

@@ -503,6 +503,7 @@ __device__ __forceinline__ bool hull_face(int shape, int face) {
 // mirror boxes meet, in FP32) is ended as lost after kMaxStuck of them.
 constexpr int kNoPrim = 0x00FFFFFF;
 constexpr int kPrimMask = 0x00FFFFFF;
+static_assert(TP_MAX_PRIMS < kNoPrim, "primitive indices must fit below kNoPrim");
 constexpr int kLastHull = 0x40000000;
 constexpr int kStuckShift = 24;
 constexpr int kStuckMask = 0x3F << kStuckShift;
