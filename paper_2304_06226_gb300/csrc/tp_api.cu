@@ -116,6 +116,7 @@ struct tp_scene {
   // divergent guns or an aperture), 0 if the lean build serves it
   int full = 1;
   int full_needed = 1;   // what the description needs (full may be forced by a test flag)
+  int src_free = 0;      // every source point in the world region (set with the tables)
   // description (owned copies)
   int world_shape = TP_BOX;
   double world_c[3] = {0, 0, 0}, world_p[3] = {0, 0, 0};
@@ -339,6 +340,29 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 // ---------------------------------------------------------------------------
 // Bounding radius about the centre over every instance, with a margin, and
 // the lists of touching primitives (boxes grown by a tolerance intersect).
+// True if no point of the box [lo, hi] is within m of primitive p (instance
+// inst): apart from its bounding box, or -- for tubes and spheres -- wholly
+// beyond the outer radius or wholly inside the inner one (a detector ring
+// around the source).
+bool box_clear_of(const tp_scene* s, const tp_prim& p, int inst, const double lo[3], const double hi[3], double m) {
+  const Box3 b = aabb(s, p, inst);
+  for (int k = 0; k < 3; ++k)
+    if (hi[k] + m < b.lo[k] || lo[k] - m > b.hi[k]) return true;
+  if (p.shape == TP_BOX) return false;
+  // nearest and farthest distance of the box from the centre (sphere) or the axis (tube)
+  double near2 = 0, far2 = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (p.shape == TP_TUBE && k == p.axis) continue;
+    const double a = lo[k] - p.centre[k], c = hi[k] - p.centre[k];
+    const double nk = (a <= 0 && c >= 0) ? 0.0 : std::min(std::fabs(a), std::fabs(c));
+    const double fk = std::max(std::fabs(a), std::fabs(c));
+    near2 += nk * nk;
+    far2 += fk * fk;
+  }
+  const double r0 = bound_r0(s, p, inst), r1 = bound_r1(s, p, inst);
+  return std::sqrt(near2) >= r1 + m || (r0 > 0 && std::sqrt(far2) <= r0 - m);
+}
+
 void neighbours(const tp_scene* s, std::vector<double>& bound, std::vector<int>& off, std::vector<int>& cnt,
                 std::vector<int>& list) {
   const int np = (int)s->prims.size();
@@ -368,21 +392,64 @@ void neighbours(const tp_scene* s, std::vector<double>& bound, std::vector<int>&
   list.clear();
   for (int i = 0; i < np; ++i) {
     off[i] = (int)list.size();
+    // i's box grown by more than the nudge past a surface: the point just
+    // outside i lies in it
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      const double tol = 1e-4 * std::max({1.0, std::fabs(box[i].lo[k]), std::fabs(box[i].hi[k])});
+      lo[k] = box[i].lo[k] - tol;
+      hi[k] = box[i].hi[k] + tol;
+    }
     for (int j = 0; j < np; ++j) {
       if (j == i) continue;
-      bool touch = true;
-      for (int k = 0; k < 3; ++k) {
-        const double tol = 1e-4 * std::max({1.0, std::fabs(box[i].lo[k]), std::fabs(box[i].hi[k])});
-        if (box[j].lo[k] > box[i].hi[k] + tol || box[j].hi[k] < box[i].lo[k] - tol) touch = false;
-      }
+      // j may hold that point unless its solid keeps clear of the grown box
+      // for every instance (apart, or -- a ring or shell about i -- i's box in
+      // its hole)
+      bool touch = false;
+      for (int q = 0; q < ninst && !touch; ++q) touch = !box_clear_of(s, s->prims[j], q, lo, hi, 0.0);
       if (touch) list.push_back(j);
     }
     cnt[i] = (int)list.size() - off[i];
   }
 }
 
+// True if every point the gun can start a neutron at -- the rectangle centre
+// +- half at the source plane, or the pencil's point -- lies inside the world
+// and outside the bounding box of every primitive (every instance), with a
+// margin far above the transport precision's rounding: the source volume is
+// then the world region without a point location.
+bool source_in_free_space(const tp_scene* s) {
+  const tp_source& g = s->source;
+  double lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) lo[k] = hi[k] = g.centre[k];
+  if (g.kind != TP_SRC_PENCIL)
+    for (int k = 0; k < 2; ++k) { lo[k] -= g.half[k]; hi[k] += g.half[k]; }
+  double scale = 1.0;
+  for (int k = 0; k < 3; ++k) scale = std::max({scale, std::fabs(lo[k]), std::fabs(hi[k])});
+  const double m = 1e-4 * scale;
+  if (s->world_shape == TP_BOX) {
+    for (int k = 0; k < 3; ++k)
+      if (lo[k] - m <= s->world_c[k] - s->world_p[k] || hi[k] + m >= s->world_c[k] + s->world_p[k]) return false;
+  } else {
+    double f2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double e = std::max(std::fabs(lo[k] - s->world_c[k]), std::fabs(hi[k] - s->world_c[k])) + m;
+      f2 += e * e;
+    }
+    if (std::sqrt(f2) >= s->world_p[1]) return false;
+  }
+  bool moving = false;
+  for (const auto& p : s->prims) moving |= (p.bind_rmin || p.bind_rmax);
+  const int ninst = moving ? s->n_inst : 1;
+  for (const auto& p : s->prims)
+    for (int q = 0; q < ninst; ++q)
+      if (!box_clear_of(s, p, q, lo, hi, m)) return false;
+  return true;
+}
+
 template <typename R>
 std::vector<uint8_t> build_blob(tp_scene* s) {
+  s->src_free = source_in_free_space(s) ? 1 : 0;
   const int np = (int)s->prims.size(), nm = (int)s->mats.size(), nmir = (int)s->mirrors.size(),
             nch = (int)s->choppers.size(), nt = (int)s->tallies.size();
   int nl = 0;
@@ -621,6 +688,7 @@ void fill_common(const tp_scene* s, KParams<R>& k) {
   k.src_slit_half[0] = (R)src.slit_half[0];
   k.src_slit_half[1] = (R)src.slit_half[1];
   k.src_kT = (R)(kBoltzmann_meV * src.temperature);
+  k.src_free = s->src_free;
   k.event_cap = s->event_cap;
   k.use_grid = s->grid_cells > 0 ? 1 : 0;
   for (int i = 0; i < 3; ++i) {

@@ -94,6 +94,7 @@ struct KParams {
   int src_kind, src_aperture;
   R src_c[3], src_half[2], src_lam_lo, src_lam_hi, src_div[2], src_ap[2];
   R src_slit_z, src_slit_half[2], src_kT;   // moderator slit; kT in meV (0: uniform wavelength)
+  int src_free;   // 1: every source point lies in the world region, outside every primitive (no locate)
   // uniform grid over the primitives (large scenes): cell (i,j,k) lists the
   // primitives whose bounding box meets it, in CSR form (grid_start / grid_items)
   int use_grid;

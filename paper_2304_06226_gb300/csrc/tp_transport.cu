@@ -732,7 +732,7 @@ __device__ bool source(const KParams<R>& kp, const View<R>& V, Particle<R>& P, R
     *end = END_APERTURE;
     return false;
   }
-  P.vol = locate(kp, V, dR, P.x);
+  P.vol = kp.src_free ? -1 : locate(kp, V, dR, P.x);
   if (P.vol == -2) { *end = END_LOST; return false; }
   if (P.vol >= 0 && V.prims[P.vol].role != TP_ROLE_BULK) { *end = END_BLACK; return false; }
   return true;
