@@ -554,27 +554,51 @@ __device__ __forceinline__ R mirror_R(const DMirror<R>& m, R Q) {
 // ---------------------------------------------------------------------------
 // Scoring: warp-aggregated FP64 atomics
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void agg_add2(double* a, double* b, unsigned long long idx, R v, R v2) {
-  const unsigned am = __activemask();
-  const unsigned grp = __match_any_sync(am, idx);
-  const int lane = threadIdx.x & 31;
-  if (__any_sync(am, __popc(grp) > 1)) {
-    // lanes on the same bin pre-sum in the transport precision (the FP64
-    // pipe is a small fraction of the FP32 one); the tally adds in FP64
-    R s = R(0), s2 = R(0);
-    unsigned m = am;
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const R x = __shfl_sync(am, v, src);
-      const R y = __shfl_sync(am, v2, src);
-      if ((grp >> src) & 1u) { s += x; s2 += y; }
-    }
-    v = s;
-    v2 = s2;
+// The active lanes that score the same bin at once: each lane's group of
+// lanes with the same bin index, the next member above it in lane order (-1
+// for the last), and the rounds a pointer-jumping sum over the largest group
+// takes (ceil log2 of its size; 0 when no two lanes share a bin).
+struct AggGroup {
+  unsigned am, grp;
+  int next, rounds;
+};
+
+__device__ __forceinline__ AggGroup agg_group(unsigned long long idx) {
+  AggGroup g;
+  g.am = __activemask();
+  g.grp = __match_any_sync(g.am, idx);
+  const unsigned gmax = __reduce_max_sync(g.am, (unsigned)__popc(g.grp));
+  g.rounds = gmax > 1u ? 32 - __clz((int)(gmax - 1u)) : 0;
+  g.next = -1;
+  if (g.rounds) {
+    const unsigned above = g.grp & (0xFFFFFFFEu << (threadIdx.x & 31));
+    if (above) g.next = __ffs(above) - 1;
   }
-  if (lane == __ffs(grp) - 1) {
+  return g;
+}
+
+// Adds v and v2 into bins a[idx], b[idx] (FP64) for every active lane of the
+// group G: the group's values are summed in the transport precision by pointer
+// jumping (after round k each lane holds its own value plus those of the next
+// 2^k - 1 members, so the lowest member ends with the group's sum; the FP64
+// pipe is a small fraction of the FP32 one) and its lowest lane adds them
+// with one FP64 atomic per array.
+template <typename R>
+__device__ __forceinline__ void agg_add2(const AggGroup& G, double* a, double* b, unsigned long long idx, R v,
+                                         R v2) {
+  int nx = G.next;
+  for (int k = 0; k < G.rounds; ++k) {
+    const int src = nx >= 0 ? nx : (int)(threadIdx.x & 31);
+    const R x = __shfl_sync(G.am, v, src);
+    const R y = __shfl_sync(G.am, v2, src);
+    const int nn = __shfl_sync(G.am, nx, src);
+    if (nx >= 0) {
+      v += x;
+      v2 += y;
+      nx = nn;
+    }
+  }
+  if ((int)(threadIdx.x & 31) == __ffs(G.grp) - 1) {
     atomicAdd(a + idx, (double)v);
     atomicAdd(b + idx, (double)v2);
   }
@@ -651,18 +675,21 @@ __device__ __forceinline__ void score_out(const KParams<R>& kp, const DTally<R>*
     const unsigned long long idx = (unsigned long long)inst * kp.total_bins + T.offset + b;
     const R w = w_;
     const unsigned long long stride = (unsigned long long)kp.n_inst * kp.total_bins;
+    // one grouping of the lanes on this path serves every array of the bin
     if (!secondary) {
-      agg_add2(kp.sum, kp.sumsq, idx, w, w * w);
+      const AggGroup G = agg_group(idx);
+      agg_add2(G, kp.sum, kp.sumsq, idx, w, w * w);
       if (GRAD) {
 #pragma unroll
         for (int p = 0; p < kMaxPar; ++p) {
           if (p >= kp.npar) break;
           const R g = w * A[p];
-          agg_add2(kp.J, kp.J2, p * stride + idx, g, g * g);
+          agg_add2(G, kp.J, kp.J2, p * stride + idx, g, g * g);
         }
       }
     } else if (kp.radius_par >= 0) {   // a radius-derivative secondary
-      agg_add2(kp.J, kp.J2, kp.radius_par * stride + idx, w, w * w);
+      const AggGroup G = agg_group(idx);
+      agg_add2(G, kp.J, kp.J2, kp.radius_par * stride + idx, w, w * w);
     }
   }
 }
