@@ -567,13 +567,11 @@ __device__ __forceinline__ AggGroup agg_group(unsigned long long idx) {
   AggGroup g;
   g.am = __activemask();
   g.grp = __match_any_sync(g.am, idx);
+  const int lane = threadIdx.x & 31;
+  const unsigned above = g.grp & (0xFFFFFFFEu << lane);
+  g.next = above ? __ffs(above) - 1 : -1;
   const unsigned gmax = __reduce_max_sync(g.am, (unsigned)__popc(g.grp));
   g.rounds = gmax > 1u ? 32 - __clz((int)(gmax - 1u)) : 0;
-  g.next = -1;
-  if (g.rounds) {
-    const unsigned above = g.grp & (0xFFFFFFFEu << (threadIdx.x & 31));
-    if (above) g.next = __ffs(above) - 1;
-  }
   return g;
 }
 
