@@ -34,7 +34,7 @@ POWDER_N = 100_000_000
 # executes (ncu smsp__inst_executed.sum x active lanes / histories on a small
 # case of the same launch): an implementation's count, reported beside the
 # algorithmic one below.  Measured for the powder workload's warp-pool kernel.
-EXECUTED_INST_PER_HISTORY = {"powder": 4459}
+EXECUTED_INST_PER_HISTORY = {"powder": 4455}
 # Algorithmic lane operations of the method per step type, counted from its
 # formulas (not from any kernel):
 #   every event (biased flight, Eq. eStepLength2, and weight, Eq. eWeight):
@@ -65,7 +65,7 @@ def algorithmic_ops_per_history(counters: dict) -> float:
 # batched, the two passes of a queued-secondaries step (measured on 4e6
 # histories of the same instance mix and scaled by histories: the queue grows
 # with them).
-TRAFFIC_PER_LAUNCH = {("powder", 3): 157184, ("batched", 2): 237405940610}
+TRAFFIC_PER_LAUNCH = {("powder", 3): 150016, ("batched", 2): 237655727793}
 # The tally whose integrated total defines "matched tally error" per workload
 # (each history scores it at most once).
 FIGURE_TALLY = {"powder": 0, "guide": 0, "imaging": 0, "batched": 0, "slab": 1, "total_scattering": 1,
