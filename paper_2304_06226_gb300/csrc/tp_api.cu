@@ -400,8 +400,15 @@ void neighbours(const tp_scene* s, std::vector<double>& bound, std::vector<int>&
       lo[k] = box[i].lo[k] - tol;
       hi[k] = box[i].hi[k] + tol;
     }
+    double scale = 1.0;
+    for (int k = 0; k < 3; ++k) scale = std::max(scale, std::fabs(s->prims[i].centre[k]));
     for (int j = 0; j < np; ++j) {
       if (j == i) continue;
+      // the point lies within i's bounding sphere grown by the nudge: j's
+      // bounding sphere must reach it
+      double d2 = 0;
+      for (int k = 0; k < 3; ++k) d2 += (s->prims[j].centre[k] - s->prims[i].centre[k]) * (s->prims[j].centre[k] - s->prims[i].centre[k]);
+      if (std::sqrt(d2) > bound[i] + bound[j] + 1e-4 * scale) continue;
       // j may hold that point unless its solid keeps clear of the grown box
       // for every instance (apart, or -- a ring or shell about i -- i's box in
       // its hole)
@@ -583,6 +590,24 @@ tp_status upload_grid(tp_scene* s) {
   // during the walk cannot skip a primitive
   for (int i = 0; i < np; ++i)
     for (int k = 0; k < 3; ++k) { box[i].lo[k] -= 1e-3 * h; box[i].hi[k] += 1e-3 * h; }
+  // and a sphere about each centre holding the primitive (every instance),
+  // padded alike: a cell that its box meets but its sphere misses (a box
+  // corner of a sphere, cylinder or tilted-looking box) does not list it
+  std::vector<double> ball(np, 0.0);
+  for (int i = 0; i < np; ++i) {
+    double r2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double e = std::max(box[i].hi[k] - s->prims[i].centre[k], s->prims[i].centre[k] - box[i].lo[k]);
+      r2 += e * e;
+    }
+    ball[i] = std::sqrt(r2);
+    if (s->prims[i].shape != TP_BOX) {   // a tube or sphere: its own radius bounds it more tightly
+      double rmax = 0;
+      for (int q = 0; q < ninst; ++q) rmax = std::max(rmax, bound_r1(s, s->prims[i], q));
+      const double hh = s->prims[i].shape == TP_TUBE ? s->prims[i].params[2] : 0.0;
+      ball[i] = std::min(ball[i], std::sqrt(rmax * rmax + hh * hh) + 2e-3 * h);
+    }
+  }
   long long ncell = 1;
   for (int k = 0; k < 3; ++k) {
     s->grid_n[k] = (int)std::max(1.0, std::min(256.0, std::round((hi[k] - lo[k]) / h)));
@@ -609,6 +634,16 @@ tp_status upload_grid(tp_scene* s) {
       for (int a = r[0][0]; a <= r[0][1]; ++a)
         for (int b = r[1][0]; b <= r[1][1]; ++b)
           for (int c = r[2][0]; c <= r[2][1]; ++c) {
+            const int ic[3] = {a, b, c};
+            double d2 = 0;   // squared distance from the centre to the cell
+            for (int k = 0; k < 3; ++k) {
+              const double w = (s->grid_hi[k] - s->grid_lo[k]) / s->grid_n[k];
+              const double lo = s->grid_lo[k] + ic[k] * w, hi = lo + w;
+              const double x = s->prims[i].centre[k];
+              const double e = x < lo ? lo - x : (x > hi ? x - hi : 0.0);
+              d2 += e * e;
+            }
+            if (std::sqrt(d2) > ball[i]) continue;
             const long long cell = ((long long)a * s->grid_n[1] + b) * s->grid_n[2] + c;
             if (pass == 0) count[cell + 1]++;
             else items[fill[cell]++] = i;
