@@ -49,7 +49,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // kernel carries only boxes, tubes and spheres, count / angular / PSD scorers
 // and pencil or rectangle guns, a smaller instruction footprint for the hot
 // loop.  Both builds compute the same thing for the scenes they accept.
-constexpr int kOptGrid = 1, kOptFull = 2;
+// kOptNoSec (gradient runs of the history kernel without a radius parameter,
+// chosen at launch): no radius-derivative secondary can arise, so the parking
+// place and the secondary's state drop out of the registers.
+constexpr int kOptGrid = 1, kOptFull = 2, kOptNoSec = 4;
 
 // ---------------------------------------------------------------------------
 // Precision traits
@@ -1057,7 +1060,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     R xn[3] = {P.x[0] + e * P.u[0], P.x[1] + e * P.u[1], P.x[2] + e * P.u[2]};
     const int v = locate_after(kp, V, dR, xn, from);
     P.last = (P.last & kStuckMask) | from | (hull_face(pf.shape, face) ? kLastHull : 0);
-    if (GRAD && kp.radius_par >= 0 && P.sub0 == 0u && pf.shape != TP_BOX &&
+    if (GRAD && !(OPT & kOptNoSec) && kp.radius_par >= 0 && P.sub0 == 0u && pf.shape != TP_BOX &&
         ((face == 0 && (pf.flags & F_BIND_RMAX)) || (face == 1 && (pf.flags & F_BIND_RMIN)))) {
       R n[3];
       normal(pf, P.x, face, n);
@@ -1104,7 +1107,7 @@ __device__ int cross(const KParams<R>& kp, const View<R>& V, Particle<R>& P, con
     for (int i = 0; i < 3; ++i) P.x[i] += e * P.u[i];
     return -1;
   }
-  if (GRAD && kp.radius_par >= 0 && P.sub0 == 0u && pt.shape != TP_BOX &&
+  if (GRAD && !(OPT & kOptNoSec) && kp.radius_par >= 0 && P.sub0 == 0u && pt.shape != TP_BOX &&
       ((face == 0 && (pt.flags & F_BIND_RMAX)) || (face == 1 && (pt.flags & F_BIND_RMIN)))) {
     R n[3];
     normal(pt, P.x, face, n);
@@ -2050,10 +2053,26 @@ auto with_budget(bool grad, bool hi, F&& f) {
   return f(typename Tag::template k<false, OPT, 3>());
 }
 
+// The gradient history kernel without secondaries (kOptNoSec), per budget.
+template <typename R, typename Tag, int OPT, typename F>
+auto with_budget_nosec(bool hi, F&& f) {
+  if constexpr (sizeof(R) == 4) {
+    if (hi) return f(typename Tag::template k<true, OPT | kOptNoSec, 4>());
+  }
+  return f(typename Tag::template k<true, OPT | kOptNoSec, 3>());
+}
+
+// nosec: a gradient run without a radius parameter (history kernel only).
 template <typename R, typename Tag, typename F>
-auto with_kernel(int variant, bool grad, bool grid, F&& f) {
+auto with_kernel(int variant, bool grad, bool grid, F&& f, bool nosec = false) {
   const bool hi = (variant & kVariantHighOcc) && sizeof(R) == 4;
   const bool full = (variant & kVariantFull) != 0;
+  if constexpr (std::is_same<Tag, HistTag<R>>::value) {
+    if (grad && nosec) {
+      if (full) return grid ? with_budget_nosec<R, Tag, kOptFull | kOptGrid>(hi, f) : with_budget_nosec<R, Tag, kOptFull>(hi, f);
+      return grid ? with_budget_nosec<R, Tag, kOptGrid>(hi, f) : with_budget_nosec<R, Tag, 0>(hi, f);
+    }
+  }
   if (full) return grid ? with_budget<R, Tag, kOptFull | kOptGrid>(grad, hi, f) : with_budget<R, Tag, kOptFull>(grad, hi, f);
   return grid ? with_budget<R, Tag, kOptGrid>(grad, hi, f) : with_budget<R, Tag, 0>(grad, hi, f);
 }
@@ -2064,7 +2083,7 @@ cudaError_t launch_family(const KParams<R>& p, int variant, bool grad, int grid,
   with_kernel<R, Tag>(variant, grad, p.use_grid != 0, [&](auto k) {
     decltype(k)::launch(p, grid, block, smem, st);
     return 0;
-  });
+  }, p.radius_par < 0);
   return cudaGetLastError();
 }
 
@@ -2084,8 +2103,16 @@ cudaError_t occupancy_of(const void* fn, int block, size_t smem, int* ctas) {
 
 template <typename R, typename Tag>
 cudaError_t occupancy_family(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
-  return occupancy_of(with_kernel<R, Tag>(variant, grad, use_grid, [](auto k) { return decltype(k)::fn(); }),
-                      block, smem, ctas);
+  cudaError_t e = occupancy_of(with_kernel<R, Tag>(variant, grad, use_grid, [](auto k) { return decltype(k)::fn(); }),
+                               block, smem, ctas);
+  if (e != cudaSuccess || !grad || !std::is_same<Tag, HistTag<R>>::value) return e;
+  // the build without secondaries that the same launch may take: its limit
+  // too, and the smaller occupancy of the two
+  int c2 = 0;
+  e = occupancy_of(with_kernel<R, Tag>(variant, grad, use_grid, [](auto k) { return decltype(k)::fn(); }, true),
+                   block, smem, &c2);
+  if (e == cudaSuccess && c2 < *ctas) *ctas = c2;
+  return e;
 }
 
 }  // namespace
