@@ -2067,7 +2067,7 @@ template <typename R, typename Tag, typename F>
 auto with_kernel(int variant, bool grad, bool grid, F&& f, bool nosec = false) {
   const bool hi = (variant & kVariantHighOcc) && sizeof(R) == 4;
   const bool full = (variant & kVariantFull) != 0;
-  if constexpr (std::is_same<Tag, HistTag<R>>::value) {
+  if constexpr (std::is_same<Tag, HistTag<R>>::value || std::is_same<Tag, WqTag<R>>::value) {
     if (grad && nosec) {
       if (full) return grid ? with_budget_nosec<R, Tag, kOptFull | kOptGrid>(hi, f) : with_budget_nosec<R, Tag, kOptFull>(hi, f);
       return grid ? with_budget_nosec<R, Tag, kOptGrid>(hi, f) : with_budget_nosec<R, Tag, 0>(hi, f);
@@ -2105,7 +2105,8 @@ template <typename R, typename Tag>
 cudaError_t occupancy_family(int variant, bool grad, bool use_grid, int block, size_t smem, int* ctas) {
   cudaError_t e = occupancy_of(with_kernel<R, Tag>(variant, grad, use_grid, [](auto k) { return decltype(k)::fn(); }),
                                block, smem, ctas);
-  if (e != cudaSuccess || !grad || !std::is_same<Tag, HistTag<R>>::value) return e;
+  if (e != cudaSuccess || !grad || !(std::is_same<Tag, HistTag<R>>::value || std::is_same<Tag, WqTag<R>>::value))
+    return e;
   // the build without secondaries that the same launch may take: its limit
   // too, and the smaller occupancy of the two
   int c2 = 0;
