@@ -261,8 +261,10 @@ typedef struct {
  *   secondaries are transported 1 = where they are made, while their primary
  *   waits, or 2 = queued in device memory and transported by a second pass of
  *   the plain kernel, the run going through the histories in chunks whose
- *   secondaries fit the queue (at most 2^25 records, sized at the first such
- *   run; a secondary finding the queue full is transported in place); 0 =
+ *   secondaries fit the queue (6 records per history, at most 2^31 records
+ *   of 56 bytes in FP32 and at most half the free device memory, sized at the
+ *   first such run; a secondary finding the queue full is transported in
+ *   place); 0 =
  *   chosen by the autotuner with kernel 0, else 1.  Results do not depend on
  *   the choice (each secondary has its own random numbers).
  * regroup (event kernel, plain runs): the bank is regrouped every `regroup`

@@ -847,17 +847,18 @@ cudaError_t launch_one(tp_scene* s, const LaunchCfg& c, bool grad, uint64_t seed
 // Histories a chunk of a queued-secondaries run may hold: the queue takes
 // kSecPerHistory secondaries per history (the batched powder workload makes
 // 3.5 on average); a fuller queue transports the rest in place.  Records are
-// 56 bytes in FP32, so the largest queue (2^28) holds 15 GB.
+// 56 bytes in FP32, so the largest queue (2^31) holds 120 GB: the 5.9e8
+// histories of the batched workload go through in two chunks.
 constexpr unsigned long long kSecPerHistory = 6;
-constexpr unsigned long long kSecCapMin = 1ull << 16, kSecCapMax = 1ull << 28;
+constexpr unsigned long long kSecCapMin = 1ull << 16, kSecCapMax = 1ull << 31;
 
 // The queue of secondaries for runs of up to `total` histories (allocated
 // outside any stream capture; a larger one drops the captured graph).
 tp_status ensure_sec(tp_scene* s, unsigned long long total) {
-  // at most a quarter of the free device memory
+  // at most half of the free device memory
   size_t free_b = 0, total_b = 0;
   TP_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const unsigned long long mem_cap = (unsigned long long)(free_b / 4 / particle_bytes(s->precision));
+  const unsigned long long mem_cap = (unsigned long long)(free_b / 2 / particle_bytes(s->precision));
   const unsigned long long cap = (s->test_flags & TP_TEST_SMALL_SEC_QUEUE) ? (1ull << 20) : kSecCapMax;
   unsigned long long want = kSecCapMin;
   while (want < cap && want < kSecPerHistory * total && 2 * want <= mem_cap) want <<= 1;
