@@ -28,6 +28,7 @@ TP_FP32, TP_FP64 = 0, 1
 TP_KERNEL_AUTO, TP_KERNEL_HISTORY, TP_KERNEL_EVENT, TP_KERNEL_WARPQ = 0, 1, 2, 3
 TP_MAX_PARAMS = 4
 TP_MAX_TALLIES = 16
+TP_MAX_PRIMS = 16777214
 COUNTER_NAMES = ["histories", "events", "collisions", "crossings", "truncated", "lost", "mirror_hits",
                  "secondaries"]
 END_NAMES = ["escaped", "absorbed", "detected", "black", "mirror", "truncated", "aperture", "lost"]

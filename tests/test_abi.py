@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(native):
 
 def test_struct_layout_matches_header(native, tmp_path):
     structs = ["tp_prim", "tp_mirror", "tp_chopper", "tp_tally_desc", "tp_source", "tp_scene_desc",
-               "tp_material", "tp_record", "tp_run"]
+               "tp_material", "tp_record", "tp_run", "tp_launch_info", "tp_peaks"]
     src = tmp_path / "sz.c"
     body = "".join(f'printf("%zu\\n", sizeof({s}));' for s in structs)
     src.write_text(f'#include <stdio.h>\n#include "tp.h"\nint main(void){{{body}return 0;}}\n')
@@ -65,6 +65,7 @@ def _desc(native, **kw):
 @pytest.mark.parametrize("field,value,status", [
     ("precision", 7, 1), ("world_shape", 9, 1), ("n_instances", 0, 1), ("n_tallies", 99, 1),
     ("n_params", 9, 1), ("event_cap", -1, 1),
+    ("n_prims", 16777215, 1),   # TP_MAX_PRIMS + 1: primitive indices must stay below the "none" marker
 ])
 def test_invalid_descriptions_rejected_before_device_work(native, field, value, status):
     d = _desc(native, **{field: value})
@@ -98,6 +99,7 @@ def test_null_arguments(native):
     assert N.lib.tp_run_histories(None, None) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_set_materials(None, None, 0) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_read_tallies(None, 0, 0, None, None, 0) == N.TP_ERR_INVALID_ARG
+    assert N.lib.tp_get_launch_info(None, None) == N.TP_ERR_INVALID_ARG
     assert N.lib.tp_total_bins(None) == 0
     assert N.lib.tp_get_launch_count(None) == 0
 
