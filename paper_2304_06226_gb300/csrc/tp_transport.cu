@@ -23,9 +23,10 @@
 // independent of the launch shape and of which lane ran which history.
 //
 // Tallies are FP64 sums of w and w^2 per bin (plus the score-function tallies),
-// added with warp-aggregated atomics: lanes hitting the same bin combine their
-// values with shuffles (in the transport precision) and one lane issues the
-// FP64 atomic.
+// added with warp-aggregated atomics: the lanes hitting one bin find each other
+// once per score, sum their values by pointer jumping over their group
+// (shuffles, in the transport precision) and the group's lowest lane issues one
+// FP64 atomic per array.
 #include <cuda_runtime.h>
 
 #include <cfloat>
